@@ -1,0 +1,183 @@
+/*
+ * sstep_cg.h - C ABI of a GB300 (sm_103a) library for Chebyshev-basis s-step Conjugate
+ * Gradient with Forward Gauss-Seidel (FGS) Gram solves.
+ *
+ * Method: Thomas and D'Ambra, "Inexact Gauss-Seidel Coarse Solvers for AMG and s-step CG",
+ * arXiv 2512.09642. Section 2 ("Preliminaries") defines the outer iteration on
+ * K_s(M^-1 A, r_k): a basis P, the Gram system G alpha = P^T r_k with G = P^T A P, and the
+ * update x_(k+1) = x_k + P alpha. Section 2, Definition "Chebyshev Polynomial Basis" gives the
+ * basis recurrence; Section 2, "Column scaling" the scaling d_i = (p_i^T A p_i)^-1/2 and the
+ * FGS iteration (I + L) a^(l+1) = P~^T r_k - L^T a^(l), a^(0) = 0. Section 8 gives the
+ * stopping rule ||r_k|| / ||r_0|| < tol and the Lanczos spectral estimate.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers whose name ends in _d are DEVICE pointers (CUDA global memory of the current
+ *    device); _h marks HOST pointers. Device arrays must be 16-byte aligned.
+ *  - Vectors have n double entries. Grid unknown (i, j, k) of an nx*ny*nz grid has index
+ *    i + nx * (j + ny * k).
+ *  - The caller owns every array it passes; the library never frees it. Arrays passed to a
+ *    create call are BORROWED for the handle's lifetime and must stay valid and unchanged
+ *    until sstep_cg_destroy. The handle owns its workspace.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream); every kernel
+ *    of the handle runs on it, and calls return with work possibly still queued on it,
+ *    except where a call says it synchronises.
+ *  - Errors are status codes; nothing throws or exits across the ABI. The text of the last
+ *    error on a handle is kept (sstep_cg_last_error). A CUDA error leaves the handle
+ *    unusable except for sstep_cg_destroy.
+ */
+#ifndef SSTEP_CG_H
+#define SSTEP_CG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SSTEP_API __attribute__((visibility("default")))
+#else
+#define SSTEP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sstep_cg_s* sstep_cg_t;
+
+typedef enum {
+    SSTEP_OK = 0,
+    SSTEP_ERR_INVALID_ARG = 1,     /* bad size, option, pointer or alignment */
+    SSTEP_ERR_CUDA = 2,            /* a CUDA runtime call or kernel failed */
+    SSTEP_ERR_OOM = 3,             /* workspace allocation failed */
+    SSTEP_ERR_NUMERICAL = 4,       /* NaN/Inf in the Gram system, or every column dropped */
+    SSTEP_ERR_NO_CONVERGENCE = 5,  /* max_outer reached, or the true residual stayed above tol */
+    SSTEP_ERR_TIMEOUT = 6,         /* a bounded device-side wait expired */
+    SSTEP_ERR_UNSUPPORTED = 7      /* valid request this build does not implement */
+} sstep_status;
+
+enum { SSTEP_BOUNDS_GIVEN = 0, SSTEP_BOUNDS_GERSH_LANCZOS10 = 1, SSTEP_BOUNDS_LANCZOS10 = 2 };
+enum { SSTEP_GRAM_SOLVE_FGS = 0, SSTEP_GRAM_SOLVE_CHOLESKY = 1 };
+enum { SSTEP_PRECISION_FP64 = 0, SSTEP_PRECISION_MIXED = 1 };
+enum { SSTEP_PRECOND_NONE = 0, SSTEP_PRECOND_JACOBI = 1 };
+enum { SSTEP_START_R = 0 };
+enum { SSTEP_GRAM_FORM_DIRECT = 0, SSTEP_GRAM_FORM_MOMENTS = 1 };
+
+#define SSTEP_MAX_S 32
+
+typedef struct {
+    int s;                 /* basis size, 1 <= s <= SSTEP_MAX_S (default 8) */
+    int nu;                /* FGS sweeps per Gram solve, 1 <= nu <= 10000 (default 25) */
+    double lambda_min;     /* spectral bounds of M^-1 A when bounds_mode = GIVEN */
+    double lambda_max;     /*   (0 <= lambda_min < lambda_max) */
+    int bounds_mode;       /* SSTEP_BOUNDS_*: GIVEN, or estimated at create time (Section 8) */
+    double tol;            /* relative residual ||r|| / ||r_0|| to stop at (default 1e-8) */
+    int max_outer;         /* outer-iteration limit (default 100000) */
+    int gram_solver;       /* SSTEP_GRAM_SOLVE_FGS (paper) or _CHOLESKY (baseline) */
+    int precision;         /* SSTEP_PRECISION_FP64 or _MIXED (FP32 basis, FP64 Gram/x/residual) */
+    int precond;           /* SSTEP_PRECOND_JACOBI (M = diag A) or _NONE (M = I) */
+    int basis_start;       /* SSTEP_START_R: p_0 = r_k as written in Section 2 */
+    int gram_form;         /* how G is formed: DIRECT inner products or Chebyshev MOMENTS */
+    int refresh_period;    /* MIXED: recompute r = b - A x every this many outers (>= 1) */
+    int max_refresh;       /* true-residual restarts after recursive convergence (default 3) */
+    uint64_t seed;         /* splitmix64 stream of the Lanczos start vector (default 5000) */
+    int use_graph;         /* 1: run the outer loop as a CUDA graph with a device-side while
+                              condition; 0: host loop that checks every check_every outers */
+    int check_every;       /* host loop only: outers launched between convergence checks */
+    int profile_every;     /* > 0: time each kernel of one outer iteration in every this many
+                              check intervals with CUDA events (sstep_cg_info.prof_*); 0: off */
+} sstep_cg_opts;
+
+typedef struct {
+    int outer_iters;           /* outer iterations applied (Gram solves that updated x) */
+    int refreshes;             /* true-residual restarts taken */
+    int status;                /* sstep_status of the solve */
+    double r0_norm;            /* ||b - A x_0|| */
+    double rel_res_recursive;  /* ||r_k|| / ||r_0|| of the recursively updated residual */
+    double rel_res_true;       /* ||b - A x|| / ||r_0|| recomputed at exit */
+    double lambda_min_used;    /* spectral bounds used by the basis */
+    double lambda_max_used;
+    double min_gii;            /* smallest Gram diagonal seen (breakdown diagnostic) */
+    double delta_last;         /* ||c~ - G~ a|| / ||c~|| of the last Gram solve (Section 7) */
+    float ms;                  /* device time of the solve (CUDA events on the stream) */
+    int kernel_launches;       /* kernels of this library launched by the solve */
+    float prof_ms[4];          /* profile_every > 0: summed device time of the sampled launches of
+                                  [0] Chebyshev steps, [1] Gram + FGS, [2] update, [3] residual */
+    int prof_launches[4];      /* number of sampled launches behind each prof_ms entry */
+} sstep_cg_info;
+
+/* Fills *opts with the defaults listed above (s = 8, nu = 25, tol = 1e-8, Jacobi, FGS,
+ * FP64, bounds GERSH_LANCZOS10, direct Gram, graph off, check_every 8). */
+SSTEP_API void sstep_cg_default_opts(sstep_cg_opts* opts);
+
+/* Handle over a CSR matrix (Section 2: A SPD and sparse). rowptr_d: int32[n+1],
+ * colind_d: int32[nnz], vals_d: double[nnz], nnz = rowptr[n] < 2^31, row-major, any column
+ * order. A must be symmetric positive definite with a positive diagonal (not checked beyond
+ * the diagonal sign). Computes M^-1, the spectral bounds (bounds_mode) and allocates the
+ * basis workspace ((s+1) vectors, plus an FP32 copy of vals in MIXED precision).
+ * Synchronises `stream`. */
+SSTEP_API sstep_status sstep_cg_create_csr(sstep_cg_t* handle, int64_t n, const int32_t* rowptr_d,
+                                 const int32_t* colind_d, const double* vals_d,
+                                 const sstep_cg_opts* opts, void* stream);
+
+/* Matrix-free handle over a structured grid with homogeneous Dirichlet boundaries.
+ * dim = 2 (nz must be 1) or 3. kappa_d = NULL: the unscaled Poisson stencil, diagonal 2*dim
+ * and -1 per in-grid neighbour (5- or 7-point). kappa_d = double[n] > 0: cell-centred
+ * diffusion -div(kappa grad u); an interior face between cells a, b has weight
+ * 2 ka kb / (ka + kb), a boundary face adds 2 kappa_cell to the diagonal.
+ * Synchronises `stream`. */
+SSTEP_API sstep_status sstep_cg_create_stencil(sstep_cg_t* handle, int dim, int nx, int ny, int nz,
+                                     const double* kappa_d, const sstep_cg_opts* opts,
+                                     void* stream);
+
+/* Solves A x = b from the initial guess in x_d (in: x_0, out: x). b_d, x_d: double[n].
+ * info may be NULL. Synchronises the handle's stream (it reads the convergence state).
+ * Returns SSTEP_OK when ||b - A x|| / ||b - A x_0|| < tol, SSTEP_ERR_NO_CONVERGENCE when
+ * max_outer outers or max_refresh restarts did not get there (x holds the last iterate). */
+SSTEP_API sstep_status sstep_cg_solve(sstep_cg_t handle, const double* b_d, double* x_d, sstep_cg_info* info);
+
+/* Same solve with HOST arrays b_h, x_h (double[n], pinned or pageable): copies b and x_0 to
+ * the handle's device buffers, solves, copies x back. Synchronises. */
+SSTEP_API sstep_status sstep_cg_solve_host(sstep_cg_t handle, const double* b_h, double* x_h, sstep_cg_info* info);
+
+/* Releases the handle and everything it owns (synchronises its stream). NULL is a no-op. */
+SSTEP_API sstep_status sstep_cg_destroy(sstep_cg_t handle);
+
+/* Static description of a status code. */
+SSTEP_API const char* sstep_cg_status_string(sstep_status status);
+
+/* Text of the last error recorded on the handle ("" if none). */
+SSTEP_API const char* sstep_cg_last_error(sstep_cg_t handle);
+
+/* --- operator and pipeline pieces (the solve is composed of these kernels) ----------- */
+
+/* y_d = A x_d with the handle's operator (double[n] each). */
+SSTEP_API sstep_status sstep_cg_apply(sstep_cg_t handle, const double* x_d, double* y_d);
+
+/* Chebyshev basis of Section 2 (Definition): column j of P_d (leading dimension ldp >= n,
+ * column-major, double[ldp * ncols]) receives p_j for j = 0 .. ncols-1, p_0 = r_d,
+ * with the handle's theta, sigma and M. 1 <= ncols <= SSTEP_MAX_S + 1. */
+SSTEP_API sstep_status sstep_cg_basis(sstep_cg_t handle, const double* r_d, double* P_d, int64_t ldp, int ncols);
+
+/* One Gram reduction and Gram solve on the handle's current basis and residual, as in the
+ * solve (Section 2): writes to out_h (host, double[3 * s + s * s]) the vector
+ * alpha = S a (s), the scaling d (s), c~ = S P^T r (s), and G~ = S G S (s*s, row-major).
+ * Run after sstep_cg_load_basis. Synchronises. */
+SSTEP_API sstep_status sstep_cg_gram_solve(sstep_cg_t handle, double* out_h);
+
+/* Copies a caller basis P_d (n x (s+1), leading dimension ldp; column 0 = r) into the handle's
+ * basis workspace, for sstep_cg_gram_solve. */
+SSTEP_API sstep_status sstep_cg_load_basis(sstep_cg_t handle, const double* P_d, int64_t ldp);
+
+/* Spectral bounds the handle uses (after create): lambda_min, lambda_max (host doubles). */
+SSTEP_API sstep_status sstep_cg_get_bounds(sstep_cg_t handle, double* lambda_min, double* lambda_max);
+
+/* Writes the handle's current residual r (column 0 of the basis workspace) to r_d. */
+SSTEP_API sstep_status sstep_cg_get_residual(sstep_cg_t handle, double* r_d);
+
+/* Lanczos tridiagonal of Section 8's estimate: k steps on D^-1/2 A D^-1/2 from the seeded
+ * start vector; writes alpha (k) and beta (k-1) to host arrays. Synchronises. */
+SSTEP_API sstep_status sstep_cg_lanczos(sstep_cg_t handle, int k, uint64_t seed, double* alpha_h, double* beta_h,
+                              int* steps_done);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSTEP_CG_H */

@@ -1,0 +1,431 @@
+// Fused Gram reduction + column scaling + FGS Gram solve (one launch per outer iteration).
+//
+// What it computes (arXiv 2512.09642, Section 2): G = P^T A P and c = P^T r_k for the
+// Chebyshev basis P = [p_0 .. p_(s-1)], p_0 = r_k; the scaling d_i = G_ii^-1/2 with
+// G~ = S G S, c~ = S c; nu FGS sweeps (I + L) a^(l+1) = c~ - L^T a^(l), a^(0) = 0; alpha = S a.
+//
+// How (GB300 design):
+//  * A P is never formed. With M the preconditioner of the recurrence, the basis satisfies
+//    A p_j = M (p_(j+1) + p_(j-1)) / (2 theta) + sigma M p_j (j >= 1), A p_0 = M p_1 / theta
+//    + sigma M p_0, i.e. A P = M P_+ B with P_+ = [P, p_s] and B the (s+1) x s tridiagonal
+//    change-of-basis matrix. One streaming pass over P_+ therefore reduces W = P^T M P_+
+//    (s(s+1)/2 symmetric entries + s entries against p_s) and, when M is not a multiple of I,
+//    c = P^T p_0; G = W B is assembled at the end.
+//  * Each warp owns a compile-time subset of the entries (s <= 8: all of them), so the
+//    accumulators stay in registers and each FP64 FMA is useful work.
+//  * Deterministic: fixed per-thread order, fixed butterfly, fixed order over warps, then
+//    the last block to arrive sums the per-block partials in block order.
+//  * The last block then runs the s x s work in one warp: lane j owns row j of G~, and each
+//    FGS sweep is s dependent warp-wide FMAs (a warp FP64 instruction costs the same with
+//    one active lane as with 32 on this part, so the sweep keeps all lanes busy).
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sstep {
+
+constexpr int GRAM_THREADS = 512;
+constexpr int GRAM_WARPS = GRAM_THREADS / 32;
+
+// Entry count M of one Gram pass and the number G of warp roles that split it: the smallest
+// G in {1, 2, 4, 8, 16} that keeps a role's accumulators within budget (FP64: 46 doubles;
+// mixed form: 28 compensated FP32 pairs).
+__host__ __device__ constexpr int gram_roles(int m, int budget) {
+    int g = 1;
+    while (g < 16 && (m + g - 1) / g > budget) g *= 2;
+    return g;
+}
+
+template <int S, bool DV>
+struct GramShape {
+    static constexpr int NSYM = S * (S + 1) / 2;    // p_a^T M p_b, 0 <= a <= b < S
+    static constexpr int NLAST = S;                 // p_a^T M p_S
+    static constexpr int M = NSYM + NLAST + (DV ? S : 0);
+    static constexpr int G = gram_roles(M, 46);     // warp roles, FP64 form
+    static constexpr int NSLAB = GRAM_WARPS / G;
+    static constexpr int G32 = gram_roles(M, 28);   // warp roles, mixed form
+    static constexpr int NSLAB32 = GRAM_WARPS / G32;
+};
+
+struct AB { int a, b, kind; };  // kind 0: p_a^T M p_b, 1: p_a^T p_0 (unweighted c)
+
+template <int S, bool DV>
+__host__ __device__ constexpr AB gram_entry(int e) {
+    constexpr int NSYM = S * (S + 1) / 2;
+    if (e < NSYM) {
+        int a = 0, len = S;
+        while (e >= len) { e -= len; ++a; --len; }
+        return AB{a, a + e, 0};
+    }
+    e -= NSYM;
+    if (e < S) return AB{e, S, 0};
+    e -= S;
+    return AB{e, 0, 1};
+}
+
+// Compile-time list of the entries owned by warp role Q (entries e with e % G == Q).
+template <int S, bool DV, int Q, int G_ = GramShape<S, DV>::G>
+struct RoleTable {
+    static constexpr int G = G_;
+    static constexpr int M = GramShape<S, DV>::M;
+    static constexpr int MQ = (M - Q + G - 1) / G;
+    int a[MQ > 0 ? MQ : 1], b[MQ > 0 ? MQ : 1], kind[MQ > 0 ? MQ : 1], e[MQ > 0 ? MQ : 1];
+    __host__ __device__ constexpr RoleTable() : a(), b(), kind(), e() {
+        int k = 0;
+        for (int ee = Q; ee < M; ee += G) {
+            const AB ab = gram_entry<S, DV>(ee);
+            a[k] = ab.a;
+            b[k] = ab.b;
+            kind[k] = ab.kind;
+            e[k] = ee;
+            ++k;
+        }
+    }
+};
+
+// Per-role accumulation over this thread's elements, then warp reduction and one write per
+// entry into smem[slab * M + entry] by lane 0.
+template <int S, bool DV, int Q>
+__device__ __forceinline__ void gram_role_f64(const double* __restrict__ P, int64_t ld, const double* __restrict__ diag,
+                                              int64_t n, int64_t e0, int64_t stride, double* smem, int slab) {
+    constexpr int G = GramShape<S, DV>::G;
+    constexpr int M = GramShape<S, DV>::M;
+    constexpr int MQ = (M - Q + G - 1) / G;
+    constexpr RoleTable<S, DV, Q> RT{};
+    double acc[MQ > 0 ? MQ : 1];
+#pragma unroll
+    for (int k = 0; k < MQ; ++k) acc[k] = 0.0;
+    for (int64_t e = e0; e < n; e += stride) {
+        double pv[S + 1];
+#pragma unroll
+        for (int c = 0; c <= S; ++c) pv[c] = __ldg(P + c * ld + e);
+        double dq[S];
+        if constexpr (DV) {
+            const double dv = __ldg(diag + e);
+#pragma unroll
+            for (int a = 0; a < S; ++a) dq[a] = dv * pv[a];
+        } else {
+#pragma unroll
+            for (int a = 0; a < S; ++a) dq[a] = pv[a];
+        }
+#pragma unroll
+        for (int k = 0; k < MQ; ++k)
+            acc[k] = fma(RT.kind[k] == 0 ? dq[RT.a[k]] : pv[RT.a[k]], pv[RT.b[k]], acc[k]);
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < MQ; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) smem[slab * M + RT.e[k]] = v;
+    }
+}
+
+template <int S, bool DV, int Q = 0>
+__device__ __forceinline__ void gram_role_dispatch(int q, const double* P, int64_t ld, const double* diag, int64_t n,
+                                                   int64_t e0, int64_t stride, double* smem, int slab) {
+    if constexpr (Q < GramShape<S, DV>::G) {
+        if (q == Q) gram_role_f64<S, DV, Q>(P, ld, diag, n, e0, stride, smem, slab);
+        else gram_role_dispatch<S, DV, Q + 1>(q, P, ld, diag, n, e0, stride, smem, slab);
+    }
+}
+
+// Mixed form: P holds FP32 vectors. Each product p_a p_b is formed exactly (FMA-based
+// TwoProduct) and summed per thread in a compensated FP32 pair (Dot2 of Ogita, Rump and
+// Oishi, about 48 significant bits); the per-thread sums are converted exactly to FP64 and
+// all further reduction (warps, blocks, grid) is in FP64.
+template <int S, bool DV, int Q>
+__device__ __forceinline__ void gram_role_f32(const float* __restrict__ P, int64_t ld, const float* __restrict__ diag,
+                                              int64_t n, int64_t e0, int64_t stride, double* smem, int slab) {
+    constexpr int G = GramShape<S, DV>::G32;
+    constexpr int M = GramShape<S, DV>::M;
+    constexpr int MQ = (M - Q + G - 1) / G;
+    constexpr RoleTable<S, DV, Q, G> RT{};
+    float ah[MQ > 0 ? MQ : 1], al[MQ > 0 ? MQ : 1];
+#pragma unroll
+    for (int k = 0; k < MQ; ++k) ah[k] = al[k] = 0.f;
+    for (int64_t e = e0; e < n; e += stride) {
+        float pv[S + 1];
+#pragma unroll
+        for (int c = 0; c <= S; ++c) pv[c] = __ldg(P + c * ld + e);
+        float dq[S];
+        if constexpr (DV) {
+            const float dv = __ldg(diag + e);
+#pragma unroll
+            for (int a = 0; a < S; ++a) dq[a] = __fmul_rn(dv, pv[a]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < S; ++a) dq[a] = pv[a];
+        }
+#pragma unroll
+        for (int k = 0; k < MQ; ++k) dot2_acc(RT.kind[k] == 0 ? dq[RT.a[k]] : pv[RT.a[k]], pv[RT.b[k]], ah[k], al[k]);
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < MQ; ++k) {
+        const double v = warp_sum(f2d_exact(ah[k]) + f2d_exact(al[k]));
+        if (lane == 0) smem[slab * M + RT.e[k]] = v;
+    }
+}
+
+template <int S, bool DV, int Q = 0>
+__device__ __forceinline__ void gram_role_dispatch32(int q, const float* P, int64_t ld, const float* diag, int64_t n,
+                                                     int64_t e0, int64_t stride, double* smem, int slab) {
+    if constexpr (Q < GramShape<S, DV>::G32) {
+        if (q == Q) gram_role_f32<S, DV, Q>(P, ld, diag, n, e0, stride, smem, slab);
+        else gram_role_dispatch32<S, DV, Q + 1>(q, P, ld, diag, n, e0, stride, smem, slab);
+    }
+}
+
+struct GramParams {
+    int nu, solver;
+    int check;                   // 1: convergence / max-outer test on c_0 = ||r_k||^2 (FP64 form);
+                                 // 0: done by the FP64 residual refresh (mixed form)
+    double theta, sigma, dfac;   // dfac: constant diagonal of M (1 when M = I); unused if DV
+};
+
+// The s x s work of one outer iteration, executed by warp 0 of the last block.
+// tot[]: reduced entries (layout of gram_entry). Writes ctl.
+template <int S, bool DV>
+__device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, double* sm /* >= S*S + 4*S doubles */) {
+    const int lane = threadIdx.x;   // warp 0 only
+    constexpr int NSYM = S * (S + 1) / 2;
+    double* Gs = sm;                // G~, row-major S x S
+    double* cs = sm + S * S;        // c~
+    double* ds = cs + S;            // d
+    double* as = ds + S;            // a (scaled solution) then alpha
+    auto Wsym = [&](int a, int b) -> double {   // p_a^T M p_b for a, b < S
+        if (a > b) { const int t = a; a = b; b = t; }
+        return tot[a * S - a * (a - 1) / 2 + (b - a)];
+    };
+    auto W = [&](int i, int k) -> double { return k < S ? Wsym(i, k) : tot[NSYM + i]; };
+    const double h0 = 1.0 / gp.theta, h1 = 0.5 / gp.theta;
+    const double sc = DV ? 1.0 : gp.dfac;
+    // G (lower triangle, mirrored) and c
+    for (int idx = lane; idx < S * S; idx += 32) {
+        const int i = idx / S, j = idx % S;
+        const int ii = i >= j ? i : j, jj = i >= j ? j : i;  // compute from the lower triangle
+        double g = gp.sigma * W(ii, jj);
+        const double hj = jj == 0 ? h0 : h1;
+        double nb = W(ii, jj + 1);
+        if (jj >= 1) nb += W(ii, jj - 1);
+        g = fma(hj, nb, g);
+        Gs[idx] = sc * g;
+    }
+    if (lane < S) cs[lane] = DV ? tot[NSYM + S + lane] : Wsym(lane, 0);
+    __syncwarp();
+    const double rk_sq = cs[0];
+    if (lane == 0) {
+        int done = RUNNING;
+        if (!(rk_sq >= 0.0) || !isfinite(rk_sq)) done = NUMERICAL;
+        if (gp.check) {
+            ctl->rk_sq = rk_sq;
+            if (done == RUNNING && (ctl->r0_sq == 0.0 || rk_sq < ctl->tol_sq * ctl->r0_sq)) done = CONVERGED;
+            else if (done == RUNNING && ctl->outer >= ctl->max_outer) done = MAX_OUTER;
+        } else if (done == RUNNING && rk_sq == 0.0) {
+            done = CONVERGED;   // the refreshed residual rounded to zero in FP32
+        }
+        ctl->done = done;
+    }
+    __syncwarp();
+    if (ctl->done != RUNNING) return;
+    // column scaling (Section 2, "Column scaling")
+    double gjj = lane < S ? Gs[lane * S + lane] : 0.0;
+    const bool keep = lane < S && gjj > 0.0 && isfinite(gjj);
+    const double dj = keep ? 1.0 / sqrt(gjj) : 0.0;
+    if (lane < S) ds[lane] = dj;
+    double mg = lane < S ? gjj : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mg = fmin(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+    const unsigned kept = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();
+    for (int idx = lane; idx < S * S; idx += 32) Gs[idx] = ds[idx / S] * Gs[idx] * ds[idx % S];
+    if (lane < S) cs[lane] = dj * cs[lane];
+    __syncwarp();
+    bool finite = true;
+    for (int idx = lane; idx < S * S; idx += 32) finite &= (bool)isfinite(Gs[idx]);
+    if (lane < S) finite &= (bool)isfinite(cs[lane]);
+    finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) ctl->min_gii = fmin(ctl->min_gii, mg);
+    if (kept == 0u || !finite) {
+        if (lane == 0) ctl->done = NUMERICAL;
+        return;
+    }
+    double a = 0.0;   // a_lane
+    if (gp.solver == SSTEP_GRAM_SOLVE_FGS) {
+        // row lane of G~ normalised by its diagonal: a_j = c^_j - sum_{i != j} G^_ji a_i
+        const double gd = lane < S ? Gs[lane * S + lane] : 1.0;
+        const bool kj = (kept >> lane) & 1u;
+        const double inv = kj ? 1.0 / gd : 0.0;
+        double grow[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) grow[i] = lane < S ? Gs[lane * S + i] * inv : 0.0;
+        const double chat = lane < S ? cs[lane] * inv : 0.0;
+        double u = chat, v = chat;
+        for (int sweep = 0; sweep < gp.nu; ++sweep) {
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                double ai = __shfl_sync(0xffffffffu, u, i);
+                if (!((kept >> i) & 1u)) ai = 0.0;
+                if (lane == i) a = ai;
+                double w = lane > i ? u : v;
+                w = fma(-grow[i], ai, w);
+                if (lane > i) u = w;
+                else if (lane < i) v = w;
+            }
+            u = v;
+            v = chat;
+        }
+    } else {
+        // Cholesky of the kept block of G~ (lane 0, sequential), the O(s^3) baseline.
+        double* R = sm + S * S + 4 * S;   // S*S scratch
+        if (lane == 0) {
+            bool ok = true;
+            for (int j = 0; j < S && ok; ++j) {
+                if (!((kept >> j) & 1u)) continue;
+                double accd = Gs[j * S + j];
+                for (int k = 0; k < j; ++k)
+                    if ((kept >> k) & 1u) accd -= R[k * S + j] * R[k * S + j];
+                if (!(accd > 0.0)) { ok = false; break; }
+                R[j * S + j] = sqrt(accd);
+                for (int i = j + 1; i < S; ++i) {
+                    if (!((kept >> i) & 1u)) continue;
+                    double t = Gs[j * S + i];
+                    for (int k = 0; k < j; ++k)
+                        if ((kept >> k) & 1u) t -= R[k * S + j] * R[k * S + i];
+                    R[j * S + i] = t / R[j * S + j];
+                }
+            }
+            if (ok) {
+                double y[S];
+                for (int i = 0; i < S; ++i) {
+                    y[i] = 0.0;
+                    if (!((kept >> i) & 1u)) continue;
+                    double t = cs[i];
+                    for (int k = 0; k < i; ++k)
+                        if ((kept >> k) & 1u) t -= R[k * S + i] * y[k];
+                    y[i] = t / R[i * S + i];
+                }
+                for (int i = S - 1; i >= 0; --i) {
+                    as[i] = 0.0;
+                    if (!((kept >> i) & 1u)) continue;
+                    double t = y[i];
+                    for (int k = i + 1; k < S; ++k)
+                        if ((kept >> k) & 1u) t -= R[i * S + k] * as[k];
+                    as[i] = t / R[i * S + i];
+                }
+            } else {
+                ctl->done = NUMERICAL;
+            }
+        }
+        __syncwarp();
+        if (ctl->done != RUNNING) return;
+        a = lane < S ? as[lane] : 0.0;
+    }
+    // inexactness delta = ||c~ - G~ a|| / ||c~|| (Section 7)
+    if (lane < S) as[lane] = a;
+    __syncwarp();
+    double res = 0.0, cn = 0.0;
+    if (lane < S) {
+        double t = cs[lane];
+        for (int i = 0; i < S; ++i) t = fma(-Gs[lane * S + i], as[i], t);
+        res = t * t;
+        cn = cs[lane] * cs[lane];
+    }
+    res = warp_sum(res);
+    cn = warp_sum(cn);
+    // alpha = S a; beta = B alpha (residual update coefficients)
+    const double al = lane < S ? ds[lane] * a : 0.0;
+    __syncwarp();
+    if (lane < S) as[lane] = al;
+    __syncwarp();
+    for (int k = lane; k <= S; k += 32) {
+        double b = k < S ? gp.sigma * as[k] : 0.0;
+        if (k >= 1) b = fma(k - 1 == 0 ? h0 : h1, as[k - 1], b);
+        if (k + 1 < S) b = fma(h1, as[k + 1], b);
+        // const M: r = sum_k gamma_k p_k with gamma_0 = 1 - m beta_0, gamma_k = -m beta_k
+        if (!DV) b = (k == 0) ? fma(-sc, b, 1.0) : -sc * b;
+        ctl->beta[k] = b;
+    }
+    if (lane < S) {
+        ctl->alpha[lane] = al;
+        ctl->d[lane] = ds[lane];
+        ctl->ct[lane] = cs[lane];
+    }
+    for (int idx = lane; idx < S * S; idx += 32) ctl->Gt[idx] = Gs[idx];
+    if (lane == 0) {
+        ctl->delta = cn > 0.0 ? sqrt(res / cn) : 0.0;
+        ctl->outer += 1;
+    }
+}
+
+template <int S, bool DV, typename T>
+__global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram(const T* __restrict__ P, int64_t ld,
+                                                         const T* __restrict__ diag, int64_t n,
+                                                         double* partials, Ctl* ctl, GramParams gp) {
+    if (ctl->done) return;
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int G = F32 ? GramShape<S, DV>::G32 : GramShape<S, DV>::G;
+    constexpr int NSLAB = F32 ? GramShape<S, DV>::NSLAB32 : GramShape<S, DV>::NSLAB;
+    constexpr int M = GramShape<S, DV>::M;
+    constexpr int NSM = (NSLAB * M) > S * S * 2 + 4 * S ? NSLAB * M : S * S * 2 + 4 * S;
+    __shared__ double smem[NSM];
+    __shared__ double tot[M];
+    __shared__ bool is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp % G, slab = warp / G;
+    const int64_t e0 = ((int64_t)blockIdx.x * NSLAB + slab) * 32 + lane;
+    const int64_t stride = (int64_t)gridDim.x * NSLAB * 32;
+    if constexpr (F32) gram_role_dispatch32<S, DV>(q, P, ld, diag, n, e0, stride, smem, slab);
+    else gram_role_dispatch<S, DV>(q, P, ld, diag, n, e0, stride, smem, slab);
+    __syncthreads();
+    for (int k = threadIdx.x; k < M; k += GRAM_THREADS) {
+        double v = 0.0;
+        for (int sl = 0; sl < NSLAB; ++sl) v += smem[sl * M + k];
+        partials[(size_t)blockIdx.x * M + k] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&ctl->counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const int nblk = gridDim.x;
+    for (int k = warp; k < M; k += GRAM_WARPS) {
+        double v = 0.0;
+        for (int b = lane; b < nblk; b += 32) v += ((volatile double*)partials)[(size_t)b * M + k];
+        v = warp_sum(v);
+        if (lane == 0) tot[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ctl->counter = 0u;
+    if (warp == 0) gram_finish<S, DV>(tot, gp, ctl, smem);
+}
+
+template <int S>
+cudaError_t launch_gram_s(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st) {
+    GramParams gp;
+    gp.nu = g.nu;
+    gp.solver = g.solver;
+    gp.check = g.fp32 ? 0 : 1;
+    gp.theta = g.theta;
+    gp.sigma = g.sigma;
+    gp.dfac = g.dconst;
+    if (g.fp32) {
+        if (g.dvec)
+            k_gram<S, true, float><<<nblocks, GRAM_THREADS, 0, st>>>((const float*)g.P, g.ld, g.diag32, g.n, partials, ctl, gp);
+        else
+            k_gram<S, false, float><<<nblocks, GRAM_THREADS, 0, st>>>((const float*)g.P, g.ld, nullptr, g.n, partials, ctl, gp);
+    } else {
+        if (g.dvec)
+            k_gram<S, true, double><<<nblocks, GRAM_THREADS, 0, st>>>((const double*)g.P, g.ld, g.diag, g.n, partials, ctl, gp);
+        else
+            k_gram<S, false, double><<<nblocks, GRAM_THREADS, 0, st>>>((const double*)g.P, g.ld, nullptr, g.n, partials, ctl, gp);
+    }
+    return cudaGetLastError();
+}
+
+
+}  // namespace sstep

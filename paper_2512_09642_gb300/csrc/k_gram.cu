@@ -1,0 +1,44 @@
+// Dispatch of the fused Gram + FGS kernel over the basis size s (instantiated in
+// k_gram_s1.cu .. k_gram_s8.cu, four values of s each, so they compile in parallel).
+#include "gram_impl.cuh"
+
+namespace sstep {
+
+#define SSTEP_EXTERN_GRAM(S) extern template cudaError_t launch_gram_s<S>(const GramArgs&, double*, Ctl*, int, cudaStream_t);
+SSTEP_EXTERN_GRAM(1) SSTEP_EXTERN_GRAM(2) SSTEP_EXTERN_GRAM(3) SSTEP_EXTERN_GRAM(4) SSTEP_EXTERN_GRAM(5)
+SSTEP_EXTERN_GRAM(6) SSTEP_EXTERN_GRAM(7) SSTEP_EXTERN_GRAM(8) SSTEP_EXTERN_GRAM(9) SSTEP_EXTERN_GRAM(10)
+SSTEP_EXTERN_GRAM(11) SSTEP_EXTERN_GRAM(12) SSTEP_EXTERN_GRAM(13) SSTEP_EXTERN_GRAM(14) SSTEP_EXTERN_GRAM(15)
+SSTEP_EXTERN_GRAM(16) SSTEP_EXTERN_GRAM(17) SSTEP_EXTERN_GRAM(18) SSTEP_EXTERN_GRAM(19) SSTEP_EXTERN_GRAM(20)
+SSTEP_EXTERN_GRAM(21) SSTEP_EXTERN_GRAM(22) SSTEP_EXTERN_GRAM(23) SSTEP_EXTERN_GRAM(24) SSTEP_EXTERN_GRAM(25)
+SSTEP_EXTERN_GRAM(26) SSTEP_EXTERN_GRAM(27) SSTEP_EXTERN_GRAM(28) SSTEP_EXTERN_GRAM(29) SSTEP_EXTERN_GRAM(30)
+SSTEP_EXTERN_GRAM(31) SSTEP_EXTERN_GRAM(32)
+#undef SSTEP_EXTERN_GRAM
+
+static int gram_m(int s, bool dvec) { return s * (s + 1) / 2 + s + (dvec ? s : 0); }
+
+int gram_blocks(const GramArgs& g, int sm_count) {
+    // one 512-thread block per SM (the kernel asks for <= 128 registers per thread),
+    // fewer when the vector is short (one element per thread of the block at most)
+    const int64_t per_block = (int64_t)GRAM_WARPS * 32;
+    int64_t want = (g.n + per_block - 1) / per_block;
+    if (want < 1) want = 1;
+    return (int)(want < sm_count ? want : sm_count);
+}
+
+size_t gram_partials_needed(const GramArgs& g, int nblocks) { return (size_t)nblocks * gram_m(g.s, g.dvec); }
+
+cudaError_t launch_gram(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st) {
+    if (g.fp32) return cudaErrorNotSupported;
+    switch (g.s) {
+#define SSTEP_CASE(S) case S: return launch_gram_s<S>(g, partials, ctl, nblocks, st);
+        SSTEP_CASE(1) SSTEP_CASE(2) SSTEP_CASE(3) SSTEP_CASE(4) SSTEP_CASE(5) SSTEP_CASE(6) SSTEP_CASE(7)
+        SSTEP_CASE(8) SSTEP_CASE(9) SSTEP_CASE(10) SSTEP_CASE(11) SSTEP_CASE(12) SSTEP_CASE(13) SSTEP_CASE(14)
+        SSTEP_CASE(15) SSTEP_CASE(16) SSTEP_CASE(17) SSTEP_CASE(18) SSTEP_CASE(19) SSTEP_CASE(20) SSTEP_CASE(21)
+        SSTEP_CASE(22) SSTEP_CASE(23) SSTEP_CASE(24) SSTEP_CASE(25) SSTEP_CASE(26) SSTEP_CASE(27) SSTEP_CASE(28)
+        SSTEP_CASE(29) SSTEP_CASE(30) SSTEP_CASE(31) SSTEP_CASE(32)
+#undef SSTEP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sstep

@@ -1,0 +1,441 @@
+// Operator kernels: the Chebyshev matrix-powers step (Section 2, Definition "Chebyshev
+// Polynomial Basis"), r = b - A x with its norm, and y = A x, for CSR matrices and for the
+// matrix-free 5-/7-point Poisson and cell-centred diffusion stencils.
+//
+// GB300 notes: FP64 issues at ~1/74 of the FP32 rate on this part, so the FP64 forms are
+// written to minimise FP64 instructions per unknown (Poisson step: 5 adds + 2 FMAs), and
+// every index is computed from the launch grid, never by 64-bit division. Stencil kernels
+// march along z with the z-neighbours held in registers; x/y neighbours come through L1.
+#include <type_traits>
+
+#include "kernels.h"
+
+namespace sstep {
+
+namespace {
+
+constexpr int BX = 32, BY = 8, KC = 8;      // stencil block (x, y) and z planes per block
+constexpr int RB = 256;                      // CSR / vector kernels: threads per block
+
+template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Face weights of the diffusion stencil in precision T.
+template <typename T> struct Faces { const T* wx; const T* wy; const T* wz; const T* diag; const T* cdinv; };
+
+// (A p)_e of the diffusion stencil split as diag_e p_e - s, with s = sum_f w_f p_nbr(f).
+template <typename T, int DIM>
+__device__ __forceinline__ T diffusion_offdiag_sum(const T* __restrict__ p, const Faces<T>& f, int64_t e, int i,
+                                                   int j, int k, int nx, int ny, int nz, int64_t sxy, T pdn, T pup) {
+    T s = (i > 0) ? ldg(f.wx + e - 1) * ldg(p + e - 1) : T(0);
+    if (i < nx - 1) s = fma(ldg(f.wx + e), ldg(p + e + 1), s);
+    if (j > 0) s = fma(ldg(f.wy + e - nx), ldg(p + e - nx), s);
+    if (j < ny - 1) s = fma(ldg(f.wy + e), ldg(p + e + nx), s);
+    if (DIM == 3) {
+        if (k > 0) s = fma(ldg(f.wz + e - sxy), pdn, s);
+        if (k < nz - 1) s = fma(ldg(f.wz + e), pup, s);
+    }
+    return s;
+}
+
+// Chebyshev step on a structured grid. POISSON: out = c1 p + c2 sum(nbrs) - q with the
+// constants folded on the host. Diffusion: out = c1 p - cdv_e s - q (Jacobi, cdv_e = c /
+// diag_e) or out = c ((diag_e - sigma) p - s) - q (no preconditioner).
+template <typename T, int DIM, bool POISSON, bool FIRST, bool JACOBI>
+__global__ void __launch_bounds__(BX* BY) k_cheb_stencil(const T* __restrict__ p, const T* __restrict__ q,
+                                                         T* __restrict__ out, int nx, int ny, int nz, Faces<T> f,
+                                                         T c1, T c2, T csig, T cscale, const Ctl* __restrict__ ctl) {
+    if (ctl->done) return;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
+    const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+    int64_t e = i + (int64_t)nx * j + sxy * k0;
+    T pdn = (DIM == 3 && k0 > 0) ? ldg(p + e - sxy) : T(0);
+    T pc = ldg(p + e);
+    for (int k = k0; k < k1; ++k, e += sxy) {
+        const T pup = (DIM == 3 && k < nz - 1) ? ldg(p + e + sxy) : T(0);
+        const T qv = FIRST ? T(0) : ldg(q + e);
+        T o;
+        if (POISSON) {
+            T s = (i > 0) ? ldg(p + e - 1) : T(0);
+            if (i < nx - 1) s += ldg(p + e + 1);
+            if (j > 0) s += ldg(p + e - nx);
+            if (j < ny - 1) s += ldg(p + e + nx);
+            if (DIM == 3) {
+                if (k > 0) s += pdn;
+                if (k < nz - 1) s += pup;
+            }
+            o = FIRST ? fma(c2, s, c1 * pc) : fma(c2, s, fma(c1, pc, -qv));
+        } else {
+            const T s = diffusion_offdiag_sum<T, DIM>(p, f, e, i, j, k, nx, ny, nz, sxy, pdn, pup);
+            if (JACOBI) {
+                T cdv = ldg(f.cdinv + e);
+                if (FIRST) cdv *= cscale;
+                o = FIRST ? fma(-cdv, s, c1 * pc) : fma(-cdv, s, fma(c1, pc, -qv));
+            } else {
+                const T t = fma(ldg(f.diag + e) - csig, pc, -s);
+                o = FIRST ? c1 * t : fma(c1, t, -qv);
+            }
+        }
+        out[e] = o;
+        pdn = pc;
+        pc = pup;
+    }
+}
+
+// CSR Chebyshev step, one thread per row: y = A p, out = cdv (y) - c sigma p - q.
+template <typename T, bool FIRST, bool JACOBI>
+__global__ void __launch_bounds__(RB) k_cheb_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                                 const T* __restrict__ vals, const T* __restrict__ cdinv,
+                                                 const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ out,
+                                                 int64_t n, T c, T csig, T cscale, const Ctl* __restrict__ ctl) {
+    if (ctl->done) return;
+    for (int64_t r = blockIdx.x * (int64_t)RB + threadIdx.x; r < n; r += (int64_t)gridDim.x * RB) {
+        const int32_t b = ldg(rowptr + r), en = ldg(rowptr + r + 1);
+        T y = T(0);
+        for (int32_t t = b; t < en; ++t) y = fma(ldg(vals + t), ldg(p + ldg(colind + t)), y);
+        T cdv = JACOBI ? ldg(cdinv + r) : c;
+        if (FIRST && JACOBI) cdv *= cscale;
+        const T pc = ldg(p + r);
+        out[r] = FIRST ? fma(cdv, y, -csig * pc) : fma(cdv, y, fma(-csig, pc, -ldg(q + r)));
+    }
+}
+
+// Block-wide sum of one double per thread, result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NT / 32; ++k) t += sh[k];
+    return t;
+}
+
+// Power of two 2^-e with rms = sqrt(sq / n) in [2^(e-1), 2^e): applied to the FP32 copy of
+// the residual so that its entries sit near 1 whatever the scale of b (mixed form).
+__device__ double pow2_scale(double sq, int64_t n) {
+    const double rms = sqrt(sq / (double)n);
+    if (!(rms > 0.0) || !isfinite(rms)) return 1.0;
+    int e = 0;
+    frexp(rms, &e);
+    return ldexp(1.0, -e);
+}
+
+// What the last block does with ||r||^2. mode 0: initial residual (r_0, and the first scale);
+// 1: true residual at exit; 2: mixed-form refresh of an outer iteration (stopping test of
+// Section 8 on the FP64 residual, scale bookkeeping).
+__device__ void residual_epilogue(Ctl* ctl, int mode, double tot, int64_t n) {
+    if (mode == 0) {
+        ctl->r0_sq = tot;
+        ctl->scale_next = pow2_scale(tot, n);
+    } else if (mode == 1) {
+        ctl->true_sq = tot;
+    } else {
+        ctl->rk_sq = tot;
+        ctl->scale = ctl->scale_next;
+        ctl->scale_next = pow2_scale(tot, n);
+        int done = RUNNING;
+        if (!isfinite(tot)) done = NUMERICAL;
+        else if (ctl->r0_sq == 0.0 || tot < ctl->tol_sq * ctl->r0_sq) done = CONVERGED;
+        else if (ctl->outer >= ctl->max_outer) done = MAX_OUTER;
+        ctl->done = done;
+    }
+}
+
+// Fixed-order sum of per-block partials by the last block to arrive (deterministic for a
+// fixed grid), then the epilogue. `counter` is reset for the next launch.
+__device__ void last_block_finish(double mine, double* partials, unsigned int* counter, Ctl* ctl, int mode,
+                                  int64_t n, int nblk) {
+    __shared__ bool last;
+    __shared__ double sh[32];
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;   // blocks may be 2D
+    if (t == 0) {
+        partials[blockIdx.x + (size_t)gridDim.x * blockIdx.y + (size_t)gridDim.x * gridDim.y * blockIdx.z] = mine;
+        __threadfence();
+        const unsigned int prev = atomicAdd(counter, 1u);
+        last = (prev == (unsigned int)nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nt = blockDim.x * blockDim.y;
+    double acc = 0.0;
+    for (int k = t; k < nblk; k += nt) acc += ((volatile double*)partials)[k];
+    acc = warp_sum(acc);
+    if ((t & 31) == 0) sh[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < nt / 32; ++k) tot += sh[k];
+        residual_epilogue(ctl, mode, tot, n);
+        *counter = 0u;
+    }
+}
+
+// r = b - A x (FP64) on the stencil, with ||r||^2.
+template <int DIM, bool POISSON>
+__global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __restrict__ b, const double* __restrict__ x,
+                                                             double* __restrict__ r, float* __restrict__ r32, int nx,
+                                                             int ny, int nz, Faces<double> f, double d2,
+                                                             double* partials, Ctl* ctl, int mode) {
+    if (mode == 2 && ctl->done) return;
+    const double scale = mode == 2 ? ctl->scale_next : 1.0;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const bool act = i < nx && j < ny;
+    double ss = 0.0;
+    if (act) {
+        const int64_t sxy = (int64_t)nx * ny;
+        const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
+        const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+        int64_t e = i + (int64_t)nx * j + sxy * k0;
+        double pdn = (DIM == 3 && k0 > 0) ? ldg(x + e - sxy) : 0.0;
+        double pc = ldg(x + e);
+        for (int k = k0; k < k1; ++k, e += sxy) {
+            const double pup = (DIM == 3 && k < nz - 1) ? ldg(x + e + sxy) : 0.0;
+            double ax;
+            if (POISSON) {
+                double s = (i > 0) ? ldg(x + e - 1) : 0.0;
+                if (i < nx - 1) s += ldg(x + e + 1);
+                if (j > 0) s += ldg(x + e - nx);
+                if (j < ny - 1) s += ldg(x + e + nx);
+                if (DIM == 3) {
+                    if (k > 0) s += pdn;
+                    if (k < nz - 1) s += pup;
+                }
+                ax = fma(d2, pc, -s);
+            } else {
+                const double s = diffusion_offdiag_sum<double, DIM>(x, f, e, i, j, k, nx, ny, nz, sxy, pdn, pup);
+                ax = fma(ldg(f.diag + e), pc, -s);
+            }
+            const double rv = ldg(b + e) - ax;
+            if (r) r[e] = rv;
+            if (r32) r32[e] = __double2float_rn(rv * scale);
+            ss = fma(rv, rv, ss);
+            pdn = pc;
+            pc = pup;
+        }
+    }
+    __shared__ double sh[BX * BY / 32];
+    // block sum over the 2D block
+    double v = warp_sum(ss);
+    const int t = threadIdx.x + BX * threadIdx.y;
+    if ((t & 31) == 0) sh[t >> 5] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (t == 0)
+        for (int k = 0; k < BX * BY / 32; ++k) tot += sh[k];
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, nblk);
+}
+
+__global__ void __launch_bounds__(RB) k_residual_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                                     const double* __restrict__ vals, const double* __restrict__ b,
+                                                     const double* __restrict__ x, double* __restrict__ r,
+                                                     float* __restrict__ r32, int64_t n, double* partials, Ctl* ctl,
+                                                     int mode) {
+    if (mode == 2 && ctl->done) return;
+    const double scale = mode == 2 ? ctl->scale_next : 1.0;
+    double ss = 0.0;
+    for (int64_t row = blockIdx.x * (int64_t)RB + threadIdx.x; row < n; row += (int64_t)gridDim.x * RB) {
+        const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
+        double y = 0.0;
+        for (int32_t t = s0; t < s1; ++t) y = fma(ldg(vals + t), ldg(x + ldg(colind + t)), y);
+        const double rv = ldg(b + row) - y;
+        if (r) r[row] = rv;
+        if (r32) r32[row] = __double2float_rn(rv * scale);
+        ss = fma(rv, rv, ss);
+    }
+    __shared__ double sh[RB / 32];
+    const double tot = block_sum<RB>(ss, sh);
+    last_block_finish(tot, partials, &ctl->counter2, ctl, mode, n, gridDim.x);
+}
+
+template <int DIM, bool POISSON>
+__global__ void __launch_bounds__(BX* BY) k_apply_stencil(const double* __restrict__ x, double* __restrict__ y, int nx,
+                                                          int ny, int nz, Faces<double> f, double d2) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
+    const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+    int64_t e = i + (int64_t)nx * j + sxy * k0;
+    double pdn = (DIM == 3 && k0 > 0) ? ldg(x + e - sxy) : 0.0;
+    double pc = ldg(x + e);
+    for (int k = k0; k < k1; ++k, e += sxy) {
+        const double pup = (DIM == 3 && k < nz - 1) ? ldg(x + e + sxy) : 0.0;
+        if (POISSON) {
+            double s = (i > 0) ? ldg(x + e - 1) : 0.0;
+            if (i < nx - 1) s += ldg(x + e + 1);
+            if (j > 0) s += ldg(x + e - nx);
+            if (j < ny - 1) s += ldg(x + e + nx);
+            if (DIM == 3) {
+                if (k > 0) s += pdn;
+                if (k < nz - 1) s += pup;
+            }
+            y[e] = fma(d2, pc, -s);
+        } else {
+            const double s = diffusion_offdiag_sum<double, DIM>(x, f, e, i, j, k, nx, ny, nz, sxy, pdn, pup);
+            y[e] = fma(ldg(f.diag + e), pc, -s);
+        }
+        pdn = pc;
+        pc = pup;
+    }
+}
+
+__global__ void __launch_bounds__(RB) k_apply_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                                  const double* __restrict__ vals, const double* __restrict__ x,
+                                                  double* __restrict__ y, int64_t n) {
+    for (int64_t row = blockIdx.x * (int64_t)RB + threadIdx.x; row < n; row += (int64_t)gridDim.x * RB) {
+        const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
+        double acc = 0.0;
+        for (int32_t t = s0; t < s1; ++t) acc = fma(ldg(vals + t), ldg(x + ldg(colind + t)), acc);
+        y[row] = acc;
+    }
+}
+
+dim3 stencil_grid(const OpDesc& op) {
+    return dim3((op.nx + BX - 1) / BX, (op.ny + BY - 1) / BY, op.dim == 3 ? (op.nz + KC - 1) / KC : 1);
+}
+
+int vec_blocks(int64_t n) {
+    int64_t b = (n + RB - 1) / RB;
+    const int64_t cap = 152 * 8;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <typename T> Faces<T> faces_of(const OpDesc& op);
+template <> Faces<double> faces_of<double>(const OpDesc& op) { return {op.wx, op.wy, op.wz, op.diag, op.cdinv}; }
+template <> Faces<float> faces_of<float>(const OpDesc& op) { return {op.wx32, op.wy32, op.wz32, op.diag32, op.cdinv32}; }
+
+template <typename T> const T* csr_vals(const OpDesc& op);
+template <> const double* csr_vals<double>(const OpDesc& op) { return op.vals; }
+template <> const float* csr_vals<float>(const OpDesc& op) { return op.vals32; }
+
+template <typename T, int DIM, bool POISSON>
+void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, double theta, double sigma, bool first,
+                           bool jacobi, const Ctl* ctl, cudaStream_t st) {
+    const dim3 grid = stencil_grid(op), block(BX, BY);
+    const double c = first ? theta : 2.0 * theta;
+    const Faces<T> f = faces_of<T>(op);
+    if (POISSON) {
+        // D^-1 A p - sigma p = (1 - sigma) p - sum / (2 dim) with Jacobi (D = 2 dim I);
+        // A p - sigma p = (2 dim - sigma) p - sum without.
+        const double d2 = 2.0 * op.dim;
+        const double c1 = jacobi ? c * (1.0 - sigma) : c * (d2 - sigma);
+        const double c2 = jacobi ? -c / d2 : -c;
+        if (first)
+            k_cheb_stencil<T, DIM, true, true, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f, (T)c1,
+                                                                           (T)c2, T(0), T(1), ctl);
+        else
+            k_cheb_stencil<T, DIM, true, false, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f, (T)c1,
+                                                                            (T)c2, T(0), T(1), ctl);
+        return;
+    }
+    if (jacobi) {
+        const double c1 = c * (1.0 - sigma);
+        if (first)
+            k_cheb_stencil<T, DIM, false, true, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f,
+                                                                            (T)c1, T(0), T(0), T(0.5), ctl);
+        else
+            k_cheb_stencil<T, DIM, false, false, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f,
+                                                                             (T)c1, T(0), T(0), T(1), ctl);
+    } else {
+        if (first)
+            k_cheb_stencil<T, DIM, false, true, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f,
+                                                                             (T)c, T(0), (T)sigma, T(1), ctl);
+        else
+            k_cheb_stencil<T, DIM, false, false, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f,
+                                                                              (T)c, T(0), (T)sigma, T(1), ctl);
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, double theta, double sigma, bool first,
+                             bool jacobi, const Ctl* ctl, cudaStream_t st) {
+    if (op.kind == OP_STENCIL) {
+        const bool poisson = op.wx == nullptr;
+        if (op.dim == 3) {
+            if (poisson) cheb_stencil_dispatch<T, 3, true>(op, p, q, out, theta, sigma, first, jacobi, ctl, st);
+            else cheb_stencil_dispatch<T, 3, false>(op, p, q, out, theta, sigma, first, jacobi, ctl, st);
+        } else {
+            if (poisson) cheb_stencil_dispatch<T, 2, true>(op, p, q, out, theta, sigma, first, jacobi, ctl, st);
+            else cheb_stencil_dispatch<T, 2, false>(op, p, q, out, theta, sigma, first, jacobi, ctl, st);
+        }
+        return cudaGetLastError();
+    }
+    const double c = first ? theta : 2.0 * theta;
+    const int nb = vec_blocks(op.n);
+    const T* cd = jacobi ? (std::is_same<T, double>::value ? (const T*)op.cdinv : (const T*)op.cdinv32) : nullptr;
+    const T* v = csr_vals<T>(op);
+    if (first) {
+        if (jacobi) k_cheb_csr<T, true, true><<<nb, RB, 0, st>>>(op.rowptr, op.colind, v, cd, p, q, out, op.n, (T)c, (T)(c * sigma), T(0.5), ctl);
+        else k_cheb_csr<T, true, false><<<nb, RB, 0, st>>>(op.rowptr, op.colind, v, cd, p, q, out, op.n, (T)c, (T)(c * sigma), T(1), ctl);
+    } else {
+        if (jacobi) k_cheb_csr<T, false, true><<<nb, RB, 0, st>>>(op.rowptr, op.colind, v, cd, p, q, out, op.n, (T)c, (T)(c * sigma), T(1), ctl);
+        else k_cheb_csr<T, false, false><<<nb, RB, 0, st>>>(op.rowptr, op.colind, v, cd, p, q, out, op.n, (T)c, (T)(c * sigma), T(1), ctl);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_cheb_step<double>(const OpDesc&, const double*, const double*, double*, double, double,
+                                              bool, bool, const Ctl*, cudaStream_t);
+template cudaError_t launch_cheb_step<float>(const OpDesc&, const float*, const float*, float*, double, double, bool,
+                                             bool, const Ctl*, cudaStream_t);
+
+size_t residual_partials_needed(const OpDesc& op) {
+    if (op.kind == OP_STENCIL) {
+        const dim3 g = stencil_grid(op);
+        return (size_t)g.x * g.y * g.z;
+    }
+    return (size_t)vec_blocks(op.n);
+}
+
+cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, double* r, float* r32,
+                            double* partials, Ctl* ctl, int mode, cudaStream_t st) {
+    if (op.kind == OP_STENCIL) {
+        const dim3 grid = stencil_grid(op), block(BX, BY);
+        const Faces<double> f = faces_of<double>(op);
+        const double d2 = 2.0 * op.dim;
+        const bool poisson = op.wx == nullptr;
+        if (op.dim == 3) {
+            if (poisson) k_residual_stencil<3, true><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
+            else k_residual_stencil<3, false><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
+        } else {
+            if (poisson) k_residual_stencil<2, true><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
+            else k_residual_stencil<2, false><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
+        }
+        return cudaGetLastError();
+    }
+    k_residual_csr<<<vec_blocks(op.n), RB, 0, st>>>(op.rowptr, op.colind, op.vals, b, x, r, r32, op.n, partials, ctl, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const OpDesc& op, const double* x, double* y, cudaStream_t st) {
+    if (op.kind == OP_STENCIL) {
+        const dim3 grid = stencil_grid(op), block(BX, BY);
+        const Faces<double> f = faces_of<double>(op);
+        const double d2 = 2.0 * op.dim;
+        const bool poisson = op.wx == nullptr;
+        if (op.dim == 3) {
+            if (poisson) k_apply_stencil<3, true><<<grid, block, 0, st>>>(x, y, op.nx, op.ny, op.nz, f, d2);
+            else k_apply_stencil<3, false><<<grid, block, 0, st>>>(x, y, op.nx, op.ny, op.nz, f, d2);
+        } else {
+            if (poisson) k_apply_stencil<2, true><<<grid, block, 0, st>>>(x, y, op.nx, op.ny, op.nz, f, d2);
+            else k_apply_stencil<2, false><<<grid, block, 0, st>>>(x, y, op.nx, op.ny, op.nz, f, d2);
+        }
+        return cudaGetLastError();
+    }
+    k_apply_csr<<<vec_blocks(op.n), RB, 0, st>>>(op.rowptr, op.colind, op.vals, x, y, op.n);
+    return cudaGetLastError();
+}
+
+}  // namespace sstep

@@ -1,0 +1,92 @@
+// Outer-iteration update (Section 2): x_(k+1) = x_k + P alpha and the residual
+// r_(k+1) = r_k - A P alpha, the latter through the change of basis A P = M P_+ B:
+// r_(k+1) = p_0 - M P_+ beta with beta = B alpha (p_0 = r_k), so A P is never stored.
+// With a constant M the Gram kernel folds M and p_0 into gamma: r_(k+1) = sum_k gamma_k p_k.
+// The new residual overwrites column 0 of P_+ in place.
+#include "kernels.h"
+
+namespace sstep {
+namespace {
+
+constexpr int UB = 256;
+
+template <bool DV>
+__global__ void __launch_bounds__(UB) k_update_f64(const double* __restrict__ P, int64_t ld, int s,
+                                                   const double* __restrict__ diag, int64_t n, double* __restrict__ x,
+                                                   double* __restrict__ r, bool skip_r, const Ctl* __restrict__ ctl) {
+    if (ctl->done) return;
+    __shared__ double al[MAXS], be[MAXC];
+    if (threadIdx.x < s) al[threadIdx.x] = ctl->alpha[threadIdx.x];
+    if (threadIdx.x <= s) be[threadIdx.x] = ctl->beta[threadIdx.x];
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)UB + threadIdx.x; e < n; e += (int64_t)gridDim.x * UB) {
+        const double p0 = __ldg(P + e);
+        double xs = fma(al[0], p0, __ldg(x + e));
+        double rs = be[0] * p0;
+#pragma unroll 4
+        for (int j = 1; j < s; ++j) {
+            const double p = __ldg(P + j * ld + e);
+            xs = fma(al[j], p, xs);
+            rs = fma(be[j], p, rs);
+        }
+        x[e] = xs;
+        if (!skip_r) {
+            rs = fma(be[s], __ldg(P + s * ld + e), rs);
+            r[e] = DV ? fma(-__ldg(diag + e), rs, p0) : rs;
+        }
+    }
+}
+
+// Mixed form (FP32 basis p^_j = scale * p_j): x += (sum_j alpha_j p^_j) / scale. alpha_j is
+// split into FP32 hi + lo; the sum over j is a compensated FP32 dot product (about 44
+// significant bits) taken in the scaled domain, where its terms are O(1), and added to x in
+// FP64 through exact conversions: one add and one FMA on the FP64 pipe per unknown.
+__global__ void __launch_bounds__(UB) k_update_mixed(const float* __restrict__ P, int64_t ld, int s, int64_t n,
+                                                     double* __restrict__ x, const Ctl* __restrict__ ctl) {
+    if (ctl->done) return;
+    __shared__ float ah[MAXS], al[MAXS];
+    if (threadIdx.x < s) {
+        const double a = ctl->alpha[threadIdx.x];
+        const float h = __double2float_rn(a);
+        ah[threadIdx.x] = h;
+        al[threadIdx.x] = __double2float_rn(a - (double)h);
+    }
+    __syncthreads();
+    const double inv_scale = 1.0 / ctl->scale;   // exact: scale is a power of two
+    for (int64_t e = blockIdx.x * (int64_t)UB + threadIdx.x; e < n; e += (int64_t)gridDim.x * UB) {
+        float sh = 0.f, sl = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < s; ++j) {
+            const float p = __ldg(P + j * ld + e);
+            dot2_acc(ah[j], p, sh, sl);
+            sl = fmaf(al[j], p, sl);
+        }
+        x[e] = fma(f2d_exact(sh) + f2d_exact(sl), inv_scale, x[e]);
+    }
+}
+
+int blocks_for(int64_t n) {
+    const int64_t b = (n + UB - 1) / UB;
+    return (int)(b < 152 * 4 ? (b < 1 ? 1 : b) : 152 * 4);
+}
+
+}  // namespace
+
+cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
+                                cudaStream_t st) {
+    k_update_mixed<<<blocks_for(n), UB, 0, st>>>(P, ld, s, n, x, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateArgs& u, const Ctl* ctl, cudaStream_t st) {
+    if (u.fp32) return cudaErrorNotSupported;
+    const double* P = (const double*)u.P;
+    double* r = (double*)u.P;   // column 0
+    if (u.dvec)
+        k_update_f64<true><<<blocks_for(u.n), UB, 0, st>>>(P, u.ld, u.s, u.diag, u.n, u.x, r, u.skip_r, ctl);
+    else
+        k_update_f64<false><<<blocks_for(u.n), UB, 0, st>>>(P, u.ld, u.s, nullptr, u.n, u.x, r, u.skip_r, ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace sstep

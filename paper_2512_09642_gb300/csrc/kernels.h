@@ -1,0 +1,101 @@
+// Host-side launchers of the library's kernels (internal; not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace sstep {
+
+// Operator description handed to kernels (plain pointers, no ownership).
+struct OpDesc {
+    int kind;            // OP_CSR or OP_STENCIL
+    int64_t n;
+    // CSR
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const double* vals;
+    const float* vals32;   // FP32 copy (mixed precision), may be null
+    // stencil
+    int dim, nx, ny, nz;
+    const double* wx;      // face weights, null for the Poisson stencil
+    const double* wy;
+    const double* wz;
+    const float* wx32;     // FP32 copies (mixed precision)
+    const float* wy32;
+    const float* wz32;
+    // diagonal of A and 2 theta / diag (null when the diagonal is the constant dconst)
+    const double* diag;
+    const double* cdinv;
+    const float* diag32;
+    const float* cdinv32;
+    double dconst;
+};
+enum { OP_CSR = 0, OP_STENCIL = 1 };
+
+// One Chebyshev step (Section 2, Definition): out = c (M^-1 A p - sigma p) - q,
+// c = theta for the first step (q absent) and 2 theta after. `first` selects the form.
+// Precision T = double (FP64) or float (mixed form basis).
+template <typename T>
+cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, double theta,
+                             double sigma, bool first, bool jacobi, const Ctl* ctl, cudaStream_t st);
+
+// r = b - A x in FP64; writes r (double, if non-null) and, if r32 != null, the FP32 copy
+// scaled by ctl->scale_next (mode 2); reduces ||r||^2 through `partials` (one double per
+// block): mode 0 -> ctl->r0_sq (initial residual), 1 -> ctl->true_sq (exit check),
+// 2 -> ctl->rk_sq plus the stopping test (mixed-form refresh; skipped once ctl->done).
+cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, double* r, float* r32,
+                            double* partials, Ctl* ctl, int mode, cudaStream_t st);
+size_t residual_partials_needed(const OpDesc& op);
+
+// y = A x (FP64).
+cudaError_t launch_apply(const OpDesc& op, const double* x, double* y, cudaStream_t st);
+
+// Gram reduction + column scaling + FGS (or Cholesky) on P_+ = [p_0 .. p_s] (FP64 or FP32
+// columns at stride ld). Per-block partials go to `partials` (gram_partials_needed doubles).
+struct GramArgs {
+    int s, nu, solver, form;
+    double theta, sigma;
+    bool dvec;                 // D is the vector op.diag (else the constant op.dconst)
+    double dconst;
+    const double* diag;
+    const float* diag32;
+    int64_t n, ld;
+    const void* P;             // column-major n x (s+1), double or float
+    bool fp32;
+};
+cudaError_t launch_gram(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st);
+int gram_blocks(const GramArgs& g, int sm_count);
+size_t gram_partials_needed(const GramArgs& g, int nblocks);
+
+// x += P alpha; r <- p_0 - D P_+ beta (written to column 0) unless skip_r.
+struct UpdateArgs {
+    int s;
+    bool dvec;
+    const double* diag;
+    int64_t n, ld;
+    const void* P;
+    bool fp32;
+    double* x;
+    bool skip_r;
+};
+cudaError_t launch_update(const UpdateArgs& u, const Ctl* ctl, cudaStream_t st);
+// Mixed form: x += P alpha / scale with FP32 P (compensated FP32 sum, exact FP64 add-in).
+cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
+                                cudaStream_t st);
+
+// Setup kernels.
+cudaError_t launch_csr_diag(const OpDesc& op, double* diag, int* bad, cudaStream_t st);
+cudaError_t launch_stencil_faces(int dim, int nx, int ny, int nz, const double* kappa, double* wx, double* wy,
+                                 double* wz, double* diag, int* bad, cudaStream_t st);
+cudaError_t launch_scale_vec(const double* diag, double c, double* out, int64_t n, cudaStream_t st);
+cudaError_t launch_rsqrt_vec(const double* diag, double* out, int64_t n, cudaStream_t st);
+cudaError_t launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t st);
+cudaError_t launch_gershgorin(const OpDesc& op, bool jacobi, double* blockmax, int nblk, cudaStream_t st);
+// Lanczos helpers on B = D^-1/2 A D^-1/2 (D^-1/2 = dhalf or a constant).
+cudaError_t launch_splitmix_uniform(uint64_t seed, double* v, int64_t n, cudaStream_t st);
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* partials, int nblk, cudaStream_t st);
+cudaError_t launch_lanczos_apply(const OpDesc& op, const double* dhalf, double dhc, const double* q, double* w,
+                                 cudaStream_t st);
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t st);
+cudaError_t launch_copy_f64(const double* src, double* dst, int64_t n, cudaStream_t st);
+
+}  // namespace sstep

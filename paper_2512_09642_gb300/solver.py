@@ -1,0 +1,98 @@
+"""SStepCG: one solver handle over a device-resident SPD system (torch tensors).
+
+A thin owner of the C handle: it keeps the borrowed device arrays alive, allocates the
+output vector and turns options into the C struct. The work is done by libsstep_cg.so.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import torch
+
+from . import abi
+
+
+class SStepCG:
+    """Chebyshev-basis s-step CG (arXiv 2512.09642, Section 2) on one CUDA device.
+
+    Exactly one of `csr=(rowptr, colind, vals)` (int32, int32, float64 CUDA tensors) or
+    `grid=(nx, ny[, nz])` (matrix-free Poisson, or diffusion with `kappa`) is given.
+    Options are the fields of sstep_cg_opts (s, nu, tol, bounds_mode, lambda_min, ...);
+    `bounds=(lmin, lmax)` is shorthand for bounds_mode="given".
+    """
+
+    def __init__(self, *, csr=None, grid=None, kappa: Optional[torch.Tensor] = None, bounds=None, stream=None,
+                 **opts):
+        if (csr is None) == (grid is None):
+            raise ValueError("give exactly one of csr= or grid=")
+        if bounds is not None:
+            opts.update(bounds_mode="given", lambda_min=float(bounds[0]), lambda_max=float(bounds[1]))
+        self.opts = abi.sstep_cg_default_opts(**opts)
+        self._keep = []
+        self.stream = stream
+        if csr is not None:
+            rowptr, colind, vals = csr
+            self._keep += [rowptr, colind, vals]
+            self.n = rowptr.numel() - 1
+            self.h = abi.sstep_cg_create_csr(self.n, rowptr, colind, vals, self.opts, stream)
+        else:
+            dims = tuple(int(v) for v in grid)
+            dim = len(dims)
+            nx, ny, nz = (dims + (1, 1))[:3]
+            if kappa is not None:
+                self._keep.append(kappa)
+            self.n = nx * ny * nz
+            self.h = abi.sstep_cg_create_stencil(dim, nx, ny, nz, kappa, self.opts, stream)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @property
+    def s(self) -> int:
+        return self.opts.s
+
+    def solve(self, b: torch.Tensor, x0: Optional[torch.Tensor] = None, allow_no_convergence: bool = True):
+        """Returns (x, info dict); x0 defaults to zeros."""
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        info = abi.sstep_cg_solve(self.h, b, x, allow=(5,) if allow_no_convergence else ())
+        return x, info.as_dict()
+
+    def solve_into(self, b: torch.Tensor, x: torch.Tensor):
+        return abi.sstep_cg_solve(self.h, b, x).as_dict()
+
+    def apply(self, x: torch.Tensor) -> torch.Tensor:
+        y = torch.empty_like(x)
+        abi.sstep_cg_apply(self.h, x, y)
+        return y
+
+    def basis(self, r: torch.Tensor, ncols: int) -> torch.Tensor:
+        """Chebyshev basis columns p_0 .. p_(ncols-1), returned as an (ncols, n) tensor."""
+        P = torch.empty((ncols, self.n), dtype=torch.float64, device=r.device)
+        abi.sstep_cg_basis(self.h, r, P, self.n, ncols)
+        return P
+
+    def gram_solve(self, P: torch.Tensor):
+        """Gram reduction + scaling + Gram solve on a given basis P ((s+1, n), row j = p_j)."""
+        abi.sstep_cg_load_basis(self.h, P.contiguous(), self.n)
+        return abi.sstep_cg_gram_solve(self.h, self.s)
+
+    def residual(self) -> torch.Tensor:
+        r = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        abi.sstep_cg_get_residual(self.h, r)
+        return r
+
+    @property
+    def bounds(self):
+        return abi.sstep_cg_get_bounds(self.h)
+
+    def lanczos(self, k: int, seed: int):
+        return abi.sstep_cg_lanczos(self.h, k, seed)
+
+    def close(self):
+        if getattr(self, "h", None):
+            abi.sstep_cg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

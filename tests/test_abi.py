@@ -1,0 +1,106 @@
+"""The C ABI without a GPU: the library loads, exports every entry point the header declares,
+the ctypes structs match the C layout (checked by compiling the header with gcc), and
+invalid arguments are rejected on the host before any CUDA call."""
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_2512_09642_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_2512_09642_gb300 import abi as mod
+    return mod
+
+
+def _declared():
+    names = set()
+    for h in HEADERS:
+        names |= set(re.findall(r"SSTEP_API\s+[\w\s\*]+?\b(sstep_\w+)\s*\(", open(h).read()))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert "sstep_cg_solve" in names and "sstep_cg_create_csr" in names and len(names) >= 10
+
+
+def test_library_exports_every_declared_symbol(abi):
+    for name in _declared():
+        assert hasattr(abi.lib, name), name
+
+
+def test_binding_covers_every_declared_symbol(abi):
+    missing = [n for n in _declared() if n not in abi.exported_names()]
+    assert not missing, missing
+
+
+def test_struct_layout_matches_c(abi):
+    import ctypes
+    fields = {"sstep_cg_opts": abi.Opts, "sstep_cg_info": abi.Info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sstep_cg.h"', "int main(void) {"]
+    for cname, cls in fields.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line)
+    for cname, cls in fields.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_default_options(abi):
+    o = abi.sstep_cg_default_opts()
+    assert (o.s, o.nu, o.tol, o.max_outer) == (8, 25, 1e-8, 100000)
+    assert o.bounds_mode == abi.BOUNDS["gersh_lanczos10"] and o.precond == abi.PRECOND["jacobi"]
+    assert o.gram_solver == abi.GRAM_SOLVER["fgs"] and o.precision == abi.PRECISION["fp64"]
+
+
+@pytest.mark.parametrize("bad", [dict(s=0), dict(s=33), dict(nu=0), dict(tol=0.0), dict(tol=-1.0),
+                                 dict(bounds_mode=0, lambda_min=1.0, lambda_max=0.5),
+                                 dict(bounds_mode=0, lambda_min=-1.0, lambda_max=2.0), dict(bounds_mode=7),
+                                 dict(gram_solver=5), dict(precond=3), dict(max_outer=-1), dict(check_every=0)])
+def test_invalid_options_rejected_on_host(abi, bad):
+    o = abi.sstep_cg_default_opts(**bad)
+    with pytest.raises(abi.SStepError) as ei:
+        abi.sstep_cg_create_stencil(2, 8, 8, 1, None, o, stream=0)
+    assert ei.value.status == 1
+    assert abi.sstep_cg_last_error(None)
+
+
+@pytest.mark.parametrize("grid", [(4, 8, 8, 1), (2, 8, 8, 2), (3, 0, 8, 8), (2, -1, 4, 1)])
+def test_invalid_grid_rejected_on_host(abi, grid):
+    with pytest.raises(abi.SStepError) as ei:
+        abi.sstep_cg_create_stencil(*grid, None, abi.sstep_cg_default_opts(), stream=0)
+    assert ei.value.status == 1
+
+
+def test_invalid_csr_rejected_on_host(abi):
+    import ctypes
+    h = ctypes.c_void_p()
+    o = abi.sstep_cg_default_opts()
+    assert abi.lib.sstep_cg_create_csr(ctypes.byref(h), 0, 16, 16, 16, ctypes.byref(o), None) == 1
+    assert abi.lib.sstep_cg_create_csr(ctypes.byref(h), 10, None, 16, 16, ctypes.byref(o), None) == 1
+    assert abi.lib.sstep_cg_create_csr(ctypes.byref(h), 10, 8, 16, 16, ctypes.byref(o), None) == 1  # misaligned
+    assert not h.value
+
+
+def test_status_strings(abi):
+    for code, name in abi.STATUS.items():
+        assert abi.sstep_cg_status_string(code) == name

@@ -1,0 +1,103 @@
+"""Mixed-precision form (FP32 basis and SpMV; FP64 Gram accumulation, FGS, x and the refreshed
+true residual) against the FP64 oracle.
+
+There is no FP32 oracle: the checks are that the solve reaches the same FP64 true relative
+residual (<= 1e-8), that its solution differs from the FP64 oracle's by no more than the
+residual tolerance allows (||x - x_o|| / ||x_o|| <= 2 kappa(A) tol, measured and printed),
+that the outer-iteration count stays close to the FP64 one, and that the first iterate agrees
+with the oracle's at FP32 level.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import spectral as OS
+from workloads import problems as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def _solver(p, mode, **opts):
+    from paper_2512_09642_gb300 import SStepCG
+    if mode == "csr":
+        rp, ci, v = p.csr()
+        return SStepCG(csr=(_dev(rp), _dev(ci), _dev(v)), **opts)
+    return SStepCG(grid=p.dims, kappa=None if p.kappa is None else _dev(p.kappa), **opts)
+
+
+CASES = [
+    ("config1_poisson2d_64_csr", W.poisson2d_64, "csr", 4, 20),
+    ("config1_poisson2d_64_stencil", W.poisson2d_64, "stencil", 4, 20),
+    ("poisson3d_32_s8", lambda: W.poisson3d(32), "stencil", 8, 25),
+    ("diffusion3d_ragged_s12", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), "stencil", 12, 30),
+    ("diffusion3d_csr_s8", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), "csr", 8, 25),
+    ("diffusion2d_stencil_s8", lambda: W.make("d2", (45, 33), kappa_sigma=0.5, config=13), "stencil", 8, 20),
+]
+
+
+@pytest.mark.parametrize("name,make,mode,s,nu", CASES, ids=[c[0] for c in CASES])
+def test_mixed_solve_reaches_fp64_tolerance(name, make, mode, s, nu):
+    p = make()
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+    ref = O.solve(op, p.b, s=s, nu=nu, lam_min=lam[0], lam_max=lam[1], tol=1e-8)
+    sv = _solver(p, mode, bounds=lam, s=s, nu=nu, tol=1e-8, precision="mixed")
+    x, info = sv.solve(_dev(p.b))
+    x = x.cpu().numpy()
+    assert info["status"] == "SSTEP_OK", info
+    true_rel = np.linalg.norm(p.b - op.matvec(x)) / np.linalg.norm(p.b)
+    assert true_rel <= 1e-8 and info["rel_res_true"] <= 1e-8
+    kA = np.linalg.cond(op.A.toarray()) if p.n <= 4096 else None
+    err = _rel(x, ref.x)
+    print(f"{name}: mixed outers {info['outer_iters']} vs fp64 oracle {ref.outer_iters}; "
+          f"|x_mixed - x_oracle| / |x_oracle| = {err:.3e}")
+    if kA is not None:
+        assert err <= 2 * kA * 1e-8
+    assert err <= 1e-4
+    assert info["outer_iters"] <= int(1.25 * ref.outer_iters) + 2
+
+
+@pytest.mark.parametrize("name,make,mode,s,nu", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_mixed_first_iterate_at_fp32_level(name, make, mode, s, nu):
+    p = make()
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+    ref = O.solve(op, p.b, s=s, nu=nu, lam_min=lam[0], lam_max=lam[1], tol=1e-30, max_outer=1, history=1)
+    sv = _solver(p, mode, bounds=lam, s=s, nu=nu, tol=1e-30, max_outer=1, precision="mixed", check_every=1)
+    x, info = sv.solve(_dev(p.b))
+    assert info["outer_iters"] == 1
+    assert _rel(x.cpu().numpy(), ref.history[0].x) <= 1e-5
+
+
+def test_mixed_is_scale_invariant():
+    """The FP32 basis is scaled by a power of two: b * 2^-120 (far below FP32's normal range
+    when unscaled) gives the same iterates times 2^-120."""
+    p = W.poisson3d(16)
+    sv = _solver(p, "stencil", s=8, nu=25, tol=1e-8, precision="mixed")
+    x1, i1 = sv.solve(_dev(p.b))
+    x2, i2 = sv.solve(_dev(p.b * 2.0 ** -120))
+    assert i1["status"] == i2["status"] == "SSTEP_OK"
+    assert i1["outer_iters"] == i2["outer_iters"]
+    assert torch.equal(x2 * 2.0 ** 120, x1)
+
+
+def test_mixed_matches_fp64_library_solution():
+    p = W.poisson3d(48)
+    sv64 = _solver(p, "stencil", s=8, nu=25, tol=1e-8)
+    sv32 = _solver(p, "stencil", s=8, nu=25, tol=1e-8, precision="mixed")
+    b = _dev(p.b)
+    x64, i64 = sv64.solve(b)
+    x32, i32 = sv32.solve(b)
+    assert i64["status"] == i32["status"] == "SSTEP_OK"
+    err = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
+    print(f"48^3: fp64 {i64['outer_iters']} outers, mixed {i32['outer_iters']}, |x32 - x64|/|x64| = {err:.2e}")
+    assert err <= 1e-5
