@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--s", type=int, default=8)
     ap.add_argument("--nu", type=int, default=25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--forms", default="fp64,mixed", help="comma list of fp64, mixed; the first is the headline")
     ap.add_argument("--cpu-outers", type=int, default=2)
     return ap.parse_args()
 
@@ -135,25 +137,39 @@ def measured_peaks():
 FP64_OPS_PEAK = 0.625e12
 
 
-def kernel_model(side, s, dim=3):
-    """Algorithmic FP64 operations and HBM bytes per unknown, per launch, for the 7-point
-    Poisson stencil path with the change-of-basis Gram (see the design notes)."""
+def kernel_model(s, mixed=False, dim=3):
+    """Algorithmic FP64-pipe operations and HBM bytes per unknown per launch, 7-point Poisson
+    stencil, change-of-basis Gram (the derivation is in the design notes)."""
     nbr = 2 * dim
+    if not mixed:
+        return {
+            # 2 dim - 1 adds of the neighbour sum + 2 FMAs; reads p_j, p_(j-1), writes p_(j+1)
+            "cheb_step": {"ops": (nbr - 1) + 2, "bytes": 24},
+            # s(s+1)/2 + s FMAs; reads the s+1 basis vectors
+            "gram_fgs": {"ops": s * (s + 1) // 2 + s, "bytes": 8 * (s + 1)},
+            # s FMAs for x, s+1 for r; reads s+1 vectors and x, writes x and r
+            "update": {"ops": 2 * s + 1, "bytes": 8 * (s + 1) + 24},
+            # A x (2 dim - 1 adds + 1 FMA), b - A x, the norm FMA; reads x, b, writes r
+            "residual": {"ops": nbr + 2, "bytes": 24},
+        }
     return {
-        # 5 adds of the neighbour sum (2 dim - 1) + 2 FMAs; reads p_j, p_(j-1), writes p_(j+1)
-        "cheb_step": {"ops": (nbr - 1) + 2, "bytes": 24},
-        # s(s+1)/2 + s FMAs; reads s+1 basis vectors
-        "gram_fgs": {"ops": s * (s + 1) // 2 + s, "bytes": 8 * (s + 1)},
-        # s FMAs for x, s+1 for r; reads s+1 vectors and x, writes x and r
-        "update": {"ops": 2 * s + 1, "bytes": 8 * (s + 1) + 24},
-        # 2 dim adds/FMAs for A x, one subtract, one FMA for the norm; reads x, b, writes r
-        "residual": {"ops": nbr + 2, "bytes": 24},
+        # FP32: no FP64 operations; reads p_j, p_(j-1), writes p_(j+1) in 4-byte words
+        "cheb_step": {"ops": 0, "bytes": 12},
+        # products and compensated sums on the FP32 pipe; reads s+1 FP32 vectors
+        "gram_fgs": {"ops": 0, "bytes": 4 * (s + 1)},
+        # one add + one FMA in FP64; reads s FP32 vectors and x, writes x
+        "update": {"ops": 2, "bytes": 4 * s + 16},
+        # FP64 residual, scale multiply, FP32 rounding; reads x, b, writes the FP32 p_0
+        "residual": {"ops": nbr + 4, "bytes": 20},
     }
 
 
-def outer_bytes(s, dim=3):
-    m = kernel_model(0, s, dim)
-    return (m["cheb_step"]["bytes"] * s - 8) + m["gram_fgs"]["bytes"] + m["update"]["bytes"]
+def outer_bytes(s, mixed=False, dim=3):
+    m = kernel_model(s, mixed, dim)
+    first = 16 if not mixed else 8    # the first step reads no p_(j-1)
+    steps = m["cheb_step"]["bytes"] * (s - 1) + first
+    extra = m["residual"]["bytes"] if mixed else 0
+    return steps + m["gram_fgs"]["bytes"] + m["update"]["bytes"] + extra
 
 
 # ---- CPU oracle timing -----------------------------------------------------------------------
@@ -235,20 +251,13 @@ def run_reference(args):
     }))
 
 
-def run_ours(args):
-    import numpy as np
+def measure_form(args, p, b, world, local, precision):
+    """Warm-up + K timed solves of one form; per-kernel durations from the sampled events."""
     import torch
-
-    world, rank, local = dist_init(args)
-    torch.cuda.set_device(local)
     from paper_2512_09642_gb300 import SStepCG, abi
-    from workloads import problems as W
 
-    side, s, nu = args.side, args.s, args.nu
-    p = W.poisson3d(side, s=s, nu=nu)
-    n = p.n
-    b = torch.as_tensor(p.b).cuda()
-    sv = SStepCG(grid=p.dims, s=s, nu=nu, tol=1e-8, check_every=8, profile_every=4)
+    n, s = p.n, args.s
+    sv = SStepCG(grid=p.dims, s=s, nu=args.nu, tol=1e-8, check_every=8, profile_every=4, precision=precision)
     stream = torch.cuda.current_stream()
 
     def one_solve():
@@ -257,7 +266,7 @@ def run_ours(args):
         return x, info.as_dict()
 
     for _ in range(args.warmup):
-        x, info = one_solve()
+        one_solve()
     clocks = ClockSampler(local)
     clocks.start()
     barrier(world)
@@ -272,85 +281,131 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    t_solve = max_over_ranks(ms / 1e3, world)
-    info = infos[-1]
-    statuses = {i["status"] for i in infos}
+    t_solve = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3, world)
 
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    bh = torch.as_tensor(p.b).pin_memory()
-    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
-    e2e_times = []
-    for _ in range(max(1, args.steps)):
-        xh.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        abi.sstep_cg_solve_host(sv.h, bh.numpy(), xh.numpy())
-        e2e_times.append(time.perf_counter() - t0)
-    t_e2e = max_over_ranks(statistics.mean(e2e_times), world)
+    t_e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI with pinned host buffers, copies inside the timed region
+        bh = torch.as_tensor(p.b).pin_memory()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        times = []
+        for _ in range(max(1, args.steps)):
+            xh.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            abi.sstep_cg_solve_host(sv.h, bh.numpy(), xh.numpy())
+            times.append(time.perf_counter() - t0)
+        t_e2e = max_over_ranks(statistics.mean(times), world)
+    sv.close()
+    return {"t": t_solve, "e2e": t_e2e, "infos": infos, "clocks": clk, "x": x}
 
-    # per-kernel durations sampled inside the timed solves (CUDA events on the solve stream)
+
+def kernel_report(args, n, infos, precision):
+    s = args.s
     names = ["cheb_step", "gram_fgs", "update", "residual"]
+    info = infos[-1]
     per_launch = {}
     for k, nm in enumerate(names):
         cnt = sum(i["prof_launches"][k] for i in infos)
         tot = sum(i["prof_ms"][k] for i in infos)
         per_launch[nm] = tot / cnt if cnt else None
     outers = info["outer_iters"]
-    launches_per_solve = {"cheb_step": s * outers, "gram_fgs": outers, "update": outers,
-                          "residual": 1 + 1 + info["refreshes"]}
-    share = {nm: (per_launch[nm] or 0.0) * launches_per_solve[nm] for nm in names}
-    dom = max(share, key=share.get)
-    model = kernel_model(side, s)
+    mixed = precision == "mixed"
+    launches = {"cheb_step": s * outers, "gram_fgs": outers, "update": outers,
+                "residual": (outers + 1 if mixed else 0) + 2 + info["refreshes"]}
+    share = {nm: (per_launch[nm] or 0.0) * launches[nm] for nm in names}
+    model = kernel_model(s, mixed)
     hbm_peak, peak_kind = measured_peaks()
-    dl = per_launch[dom] / 1e3
-    ops = model[dom]["ops"] * n
-    by = model[dom]["bytes"] * n
-    roofline = {"bound": "alu", "kernel": dom, "achieved": ops / dl / 1e9, "peak": FP64_OPS_PEAK / 1e9,
-                "unit": "G FP64-op/s", "frac": ops / dl / FP64_OPS_PEAK, "traffic": None,
-                "peak_kind": "derived from nominal 1.25 TFLOP/s FP64 (152 SMs x 2.07 GHz)",
-                "ops_per_launch": ops, "bytes_per_launch": by, "avg_launch_ms": per_launch[dom],
-                "hbm_gbs": by / dl / 1e9, "hbm_frac": by / dl / 1e9 / hbm_peak,
-                "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind}
-    kernel_table = {nm: {"avg_launch_ms": per_launch[nm], "launches_per_solve": launches_per_solve[nm],
-                         "share": share[nm] / max(sum(share.values()), 1e-30),
-                         "fp64_ops_per_s": (model[nm]["ops"] * n / (per_launch[nm] / 1e3)) if per_launch[nm] else None,
-                         "hbm_gbs": (model[nm]["bytes"] * n / (per_launch[nm] / 1e3) / 1e9) if per_launch[nm] else None}
-                    for nm in names}
-    bytes_solve = outer_bytes(s) * n * outers
-    hbm_gbs_solve = bytes_solve / t_solve / 1e9
+    table = {}
+    for nm in names:
+        d = per_launch[nm]
+        table[nm] = {"avg_launch_ms": d, "launches_per_solve": launches[nm],
+                     "share": share[nm] / max(sum(share.values()), 1e-30),
+                     "fp64_ops_per_launch": model[nm]["ops"] * n, "bytes_per_launch": model[nm]["bytes"] * n,
+                     "fp64_gops": model[nm]["ops"] * n / (d / 1e3) / 1e9 if d else None,
+                     "hbm_gbs": model[nm]["bytes"] * n / (d / 1e3) / 1e9 if d else None}
+    dom = max(share, key=share.get)
+    d = per_launch[dom] / 1e3
+    ops, by = model[dom]["ops"] * n, model[dom]["bytes"] * n
+    alu_frac = ops / d / FP64_OPS_PEAK
+    hbm_frac = by / d / 1e9 / hbm_peak
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": ops / d / 1e9, "peak": FP64_OPS_PEAK / 1e9, "unit": "G FP64-op/s",
+                "frac": alu_frac, "peak_kind": "derived: nominal 1.25 TFLOP/s FP64 = 152 SMs x 2 FP64 FMA/clk x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": by / d / 1e9, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    roof.update({"kernel": dom, "traffic": None, "avg_launch_ms": per_launch[dom], "fp64_ops_per_launch": ops,
+                 "bytes_per_launch": by, "alu_frac": alu_frac, "hbm_frac": hbm_frac})
+    return roof, table
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    from workloads import problems as W
+
+    side, s, nu = args.side, args.s, args.nu
+    p = W.poisson3d(side, s=s, nu=nu)
+    n = p.n
+    b = torch.as_tensor(p.b).cuda()
+    forms = {}
+    res = {}
+    for prec in args.forms.split(","):
+        r = measure_form(args, p, b, world, local, prec)
+        roof, table = kernel_report(args, n, r["infos"], prec)
+        info = r["infos"][-1]
+        outers = info["outer_iters"]
+        bytes_solve = outer_bytes(s, prec == "mixed") * n * outers
+        forms[prec] = {"time_s": r["t"], "outer_iters": outers, "status": sorted({i["status"] for i in r["infos"]}),
+                       "rel_res_true": info["rel_res_true"], "outer_per_s": outers / r["t"],
+                       "hbm_gbs_model": bytes_solve / r["t"] / 1e9,
+                       "model_bytes_per_outer": outer_bytes(s, prec == "mixed") * n,
+                       "e2e_s": r["e2e"], "roofline": roof, "kernels": table, "clocks": r["clocks"],
+                       "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"]))}
+        res[prec] = r
+    if "fp64" in res and "mixed" in res:
+        x64, x32 = res["fp64"]["x"], res["mixed"]["x"]
+        forms["mixed"]["speedup_vs_fp64"] = res["fp64"]["t"] / res["mixed"]["t"]
+        forms["mixed"]["rel_diff_vs_fp64_x"] = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
+        xs = torch.as_tensor(p.x_star).cuda()
+        for prec in ("fp64", "mixed"):
+            forms[prec]["rel_err_vs_xstar"] = float(torch.linalg.norm(res[prec]["x"] - xs) / torch.linalg.norm(xs))
+    head = args.forms.split(",")[0]
+    h = forms[head]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        outers = h["outer_iters"]
         try:
             per = statistics.mean(oracle_outer_times(side, s, nu, args.cpu_outers, 1)) / args.cpu_outers
             cpu = {"value": per * outers, "unit": "s", "cores": 1, "kind": "oracle", "cpu": cpu_model(),
                    "sample": f"{args.cpu_outers} outer iterations of the same {side}^3 solve on the oracle "
-                             f"(numpy/scipy, 1 thread), seconds per outer x the {outers} outer iterations "
+                             f"(numpy/scipy FP64, 1 thread), seconds per outer x the {outers} outer iterations "
                              "of the measured solve", "s_per_outer": per}
         except Exception as ex:  # the CPU leg must not hide the GPU result
             cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": t_solve * world / world, "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "metric": METRIC, "value": h["time_s"], "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["time_s"] * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head == "fp64" else "f32 basis + f64 Gram/x/residual",
             "data": "synthetic (b = A x*, x* ~ U(-1,1) splitmix64 seed 1002)",
             "config": {"workload": f"poisson3d_7pt_{side}^3", "n": n, "operator": "matrix-free stencil",
                        "s": s, "nu": nu, "precond": "jacobi", "bounds": "gershgorin + lanczos10",
-                       "tol": 1e-8, "form": "fp64", "l2": "inputs larger than L2 (P_+ = 1.2 GB)",
+                       "tol": 1e-8, "form": head, "l2": "inputs larger than L2 (P_+ = 1.2 GB)",
                        "parallelism": f"replicas x{world}"},
-            "outer_iters": outers, "status": sorted(statuses), "rel_res_true": info["rel_res_true"],
-            "outer_per_s": outers / t_solve, "hbm_gbs_model": hbm_gbs_solve,
-            "model_bytes_per_outer": outer_bytes(s) * n,
-            "roofline": roofline, "kernels": kernel_table,
-            "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
-            "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
-            "clocks": clk, "cpu_baseline": cpu,
+            "outer_iters": h["outer_iters"], "rel_res_true": h["rel_res_true"], "outer_per_s": h["outer_per_s"],
+            "hbm_gbs_model": h["hbm_gbs_model"], "roofline": h["roofline"],
+            "e2e": {"value": h["e2e_s"], "unit": "s", "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": h["gpu_launches"], "clocks": h["clocks"], "cpu_baseline": cpu, "forms": forms,
         }
         print(json.dumps(line))
-    sv.close()
 
 
 def main():

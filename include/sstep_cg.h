@@ -137,6 +137,17 @@ SSTEP_API sstep_status sstep_cg_solve(sstep_cg_t handle, const double* b_d, doub
  * the handle's device buffers, solves, copies x back. Synchronises. */
 SSTEP_API sstep_status sstep_cg_solve_host(sstep_cg_t handle, const double* b_h, double* x_h, sstep_cg_info* info);
 
+/* Differentiable solve (adjoint): for a diffusion stencil handle (created with kappa_d) and a
+ * loss L(x) with x = A(kappa)^-1 b, given x_d and the adjoint solution lambda_d of
+ * A lambda = dL/dx (A is symmetric, so the same handle's sstep_cg_solve gives it), writes
+ *   gkappa_d[c] = dL/dkappa_c = -lambda^T (dA/dkappa_c) x
+ *              = -sum_{faces (c,o)} 2 ko^2/(kc+ko)^2 (lambda_c-lambda_o)(x_c-x_o) - 2 nbf_c lambda_c x_c
+ * (nbf_c: boundary faces of cell c). dL/db = lambda. All arrays double[n] on the device.
+ * The paper has no adjoint; this is the gradient of the solve it describes (Section 2).
+ * SSTEP_ERR_INVALID_ARG for a CSR or Poisson handle. */
+SSTEP_API sstep_status sstep_cg_grad_kappa(sstep_cg_t handle, const double* x_d, const double* lambda_d,
+                                           double* gkappa_d);
+
 /* Releases the handle and everything it owns (synchronises its stream). NULL is a no-op. */
 SSTEP_API sstep_status sstep_cg_destroy(sstep_cg_t handle);
 

@@ -79,6 +79,7 @@ _SIGS = {
     "sstep_cg_get_bounds": (_I, [_VP, C.POINTER(_D), C.POINTER(_D)]),
     "sstep_cg_get_residual": (_I, [_VP, _VP]),
     "sstep_cg_lanczos": (_I, [_VP, _I, C.c_uint64, _VP, _VP, C.POINTER(_I)]),
+    "sstep_cg_grad_kappa": (_I, [_VP, _VP, _VP, _VP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -215,6 +216,10 @@ def sstep_cg_lanczos(h, k: int, seed: int):
     _check(lib.sstep_cg_lanczos(h, int(k), int(seed), a.ctypes.data, b.ctypes.data, C.byref(steps)), h)
     m = steps.value
     return a[:m].copy(), b[:max(m - 1, 0)].copy()
+
+
+def sstep_cg_grad_kappa(h, x, lam, g):
+    return _check(lib.sstep_cg_grad_kappa(h, _ptr(x), _ptr(lam), _ptr(g)), h)
 
 
 def exported_names():

@@ -24,6 +24,7 @@ struct sstep_cg_s {
     double* diag = nullptr;     // diag(A) (CSR, diffusion)
     double* cdinv = nullptr;    // 2 theta / diag (Jacobi)
     double* faces = nullptr;    // wx | wy | wz (diffusion)
+    const double* kappa = nullptr;   // borrowed per-cell coefficient (diffusion stencil)
     double* P = nullptr;        // basis P_+ = [p_0 .. p_s], column-major, leading dimension ld
     int64_t ld = 0;
     bool mixed = false;         // FP32 basis (form 1)
@@ -36,6 +37,12 @@ struct sstep_cg_s {
     Ctl* ctl = nullptr;
     Ctl* ctl_h = nullptr;       // pinned mirror
     double* bx_dev = nullptr;   // device b, x for sstep_cg_solve_host
+    // graph mode: one while-node graph per (b, x) pair, captured on cap_stream
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const double* g_b = nullptr;
+    double* g_x = nullptr;
     cudaEvent_t ev[SSTEP_MAX_S + 4] = {};   // profiling: boundaries of one outer iteration
     cudaEvent_t rev[2] = {};                // profiling: residual kernel
     char err[512] = {0};
@@ -96,7 +103,7 @@ sstep_status validate_opts(sstep_cg_t h, const sstep_cg_opts* o) {
         return SSTEP_ERR_UNSUPPORTED;
     }
     if (o->gram_form != SSTEP_GRAM_FORM_DIRECT) { set_err(h, "gram_form %d not built yet", o->gram_form); return SSTEP_ERR_UNSUPPORTED; }
-    if (o->use_graph) { set_err(h, "graph mode not built yet"); return SSTEP_ERR_UNSUPPORTED; }
+
     if (o->check_every < 1) { set_err(h, "check_every < 1"); return SSTEP_ERR_INVALID_ARG; }
     if (o->profile_every < 0) { set_err(h, "profile_every < 0"); return SSTEP_ERR_INVALID_ARG; }
     return SSTEP_OK;
@@ -470,6 +477,50 @@ sstep_status launch_residual_timed(sstep_cg_t h, const double* b, const double* 
     return SSTEP_OK;
 }
 
+void drop_graph(sstep_cg_t h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    h->g_b = nullptr;
+    h->g_x = nullptr;
+}
+
+// The outer loop as one graph: a while node whose body is one outer iteration followed by
+// k_loop_cond, which keeps the node looping while ctl->done == RUNNING. Captured on an
+// internal stream (the caller's may be the legacy stream, which cannot be captured).
+sstep_status build_graph(sstep_cg_t h, const double* b, double* x) {
+    drop_graph(h);
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaGraphCreate(&h->graph, 0));
+    cudaGraphConditionalHandle ch;
+    CK(cudaGraphConditionalHandleCreate(&ch, h->graph, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = ch;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    int dummy = 0;
+    sstep_status st = launch_outer(h, b, x, &dummy, false);
+    cudaError_t e = st == SSTEP_OK ? launch_loop_cond(ch, h->ctl, h->cap_stream) : cudaSuccess;
+    h->stream = user;
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+    if (st != SSTEP_OK) { drop_graph(h); return st; }
+    CK(e);
+    CK(e2);
+    CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    h->g_b = b;
+    h->g_x = x;
+    return SSTEP_OK;
+}
+
 sstep_status read_ctl(sstep_cg_t h) {
     CK(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -503,12 +554,23 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
     ++launches;
     sstep_status status = SSTEP_OK;
     int refreshes = 0;
+    const int outer_launches = h->opts.s + 2 + (h->mixed ? 1 : 0);
     for (long chunk = 0;; ++chunk) {
-        const bool prof = profiling && chunk % h->opts.profile_every == 0;
-        for (int m = 0; m < h->opts.check_every; ++m)
-            if ((st = launch_outer(h, b, x, &launches, prof && m == 0)) != SSTEP_OK) return st;
-        if ((st = read_ctl(h)) != SSTEP_OK) return st;
-        if (prof && (st = collect_outer_profile(h, &inf)) != SSTEP_OK) return st;
+        if (h->opts.use_graph) {
+            if (!h->gexec || h->g_b != b || h->g_x != x)
+                if ((st = build_graph(h, b, x)) != SSTEP_OK) return st;
+            const int before = h->ctl_h->outer;
+            CK(cudaGraphLaunch(h->gexec, h->stream));
+            if ((st = read_ctl(h)) != SSTEP_OK) return st;
+            // kernels that ran: every body pass launches the outer's kernels and the condition
+            launches += (h->ctl_h->outer - before + 1) * (outer_launches + 1);
+        } else {
+            const bool prof = profiling && chunk % h->opts.profile_every == 0;
+            for (int m = 0; m < h->opts.check_every; ++m)
+                if ((st = launch_outer(h, b, x, &launches, prof && m == 0)) != SSTEP_OK) return st;
+            if ((st = read_ctl(h)) != SSTEP_OK) return st;
+            if (prof && (st = collect_outer_profile(h, &inf)) != SSTEP_OK) return st;
+        }
         const int done = h->ctl_h->done;
         if (done == RUNNING) continue;
         // true residual b - A x (Section 8 stopping rule is checked on it at exit)
@@ -654,6 +716,7 @@ sstep_status sstep_cg_create_stencil(sstep_cg_t* out, int dim, int nx, int ny, i
         cudaFree(bad);
         if (e != cudaSuccess) { set_err(h, "stencil set-up: %s", cudaGetErrorString(e)); return fail_create(h, e == cudaErrorMemoryAllocation ? SSTEP_ERR_OOM : SSTEP_ERR_CUDA); }
         if (hb) { set_err(h, "kappa must be positive and finite"); return fail_create(h, SSTEP_ERR_INVALID_ARG); }
+        h->kappa = kappa_d;
     }
     st = finish_create(h);
     if (st != SSTEP_OK) return fail_create(h, st);
@@ -711,6 +774,8 @@ sstep_status sstep_cg_destroy(sstep_cg_t h) {
     cudaFree(h->res_partials);
     cudaFree(h->ctl);
     cudaFree(h->bx_dev);
+    drop_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->ctl_h) cudaFreeHost(h->ctl_h);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -802,6 +867,16 @@ sstep_status sstep_cg_get_bounds(sstep_cg_t h, double* lmin, double* lmax) {
 sstep_status sstep_cg_get_residual(sstep_cg_t h, double* r_d) {
     if (!h || !r_d) return SSTEP_ERR_INVALID_ARG;
     CK(cudaMemcpyAsync(r_d, h->P, sizeof(double) * h->op.n, cudaMemcpyDeviceToDevice, h->stream));
+    return SSTEP_OK;
+}
+
+sstep_status sstep_cg_grad_kappa(sstep_cg_t h, const double* x_d, const double* lambda_d, double* gkappa_d) {
+    if (!h || !x_d || !lambda_d || !gkappa_d) return SSTEP_ERR_INVALID_ARG;
+    if (h->op.kind != OP_STENCIL || !h->kappa) {
+        set_err(h, "sstep_cg_grad_kappa needs a diffusion stencil handle (created with kappa)");
+        return SSTEP_ERR_INVALID_ARG;
+    }
+    CK(launch_grad_kappa(h->op.dim, h->op.nx, h->op.ny, h->op.nz, h->kappa, x_d, lambda_d, gkappa_d, h->stream));
     return SSTEP_OK;
 }
 

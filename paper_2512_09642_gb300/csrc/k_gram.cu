@@ -28,7 +28,6 @@ int gram_blocks(const GramArgs& g, int sm_count) {
 size_t gram_partials_needed(const GramArgs& g, int nblocks) { return (size_t)nblocks * gram_m(g.s, g.dvec); }
 
 cudaError_t launch_gram(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st) {
-    if (g.fp32) return cudaErrorNotSupported;
     switch (g.s) {
 #define SSTEP_CASE(S) case S: return launch_gram_s<S>(g, partials, ctl, nblocks, st);
         SSTEP_CASE(1) SSTEP_CASE(2) SSTEP_CASE(3) SSTEP_CASE(4) SSTEP_CASE(5) SSTEP_CASE(6) SSTEP_CASE(7)

@@ -65,12 +65,22 @@ __global__ void __launch_bounds__(UB) k_update_mixed(const float* __restrict__ P
     }
 }
 
+// Body of the graph's while node: keep looping while the outer iteration is running.
+__global__ void k_loop_cond(cudaGraphConditionalHandle handle, const Ctl* __restrict__ ctl) {
+    cudaGraphSetConditional(handle, ctl->done == RUNNING ? 1u : 0u);
+}
+
 int blocks_for(int64_t n) {
     const int64_t b = (n + UB - 1) / UB;
     return (int)(b < 152 * 4 ? (b < 1 ? 1 : b) : 152 * 4);
 }
 
 }  // namespace
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, cudaStream_t st) {
+    k_loop_cond<<<1, 1, 0, st>>>(handle, ctl);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
                                 cudaStream_t st) {

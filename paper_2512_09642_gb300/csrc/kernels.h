@@ -82,6 +82,13 @@ cudaError_t launch_update(const UpdateArgs& u, const Ctl* ctl, cudaStream_t st);
 cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
                                 cudaStream_t st);
 
+// Sets the graph while-node condition to (ctl->done == RUNNING).
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, cudaStream_t st);
+
+// Adjoint: dL/dkappa of the diffusion stencil from x and lambda (see k_adjoint.cu).
+cudaError_t launch_grad_kappa(int dim, int nx, int ny, int nz, const double* kappa, const double* x,
+                              const double* lam, double* g, cudaStream_t st);
+
 // Setup kernels.
 cudaError_t launch_csr_diag(const OpDesc& op, double* diag, int* bad, cudaStream_t st);
 cudaError_t launch_stencil_faces(int dim, int nx, int ny, int nz, const double* kappa, double* wx, double* wy,
