@@ -368,7 +368,7 @@ sstep_status bind_device(sstep_cg_t h) {
     return SSTEP_OK;
 }
 
-// Error message buffer for failures before a handle exists.
+// Error message buffer for failures without a handle (create calls, handle-free entry points).
 thread_local char g_create_err[512];
 
 sstep_status fail_create(sstep_cg_t h, sstep_status st) {
@@ -616,6 +616,10 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
 }
 
 }  // namespace
+
+namespace sstep {
+void set_global_error(const char* msg) { std::snprintf(g_create_err, sizeof(g_create_err), "%s", msg); }
+}  // namespace sstep
 
 extern "C" {
 
