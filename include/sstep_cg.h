@@ -188,6 +188,34 @@ SSTEP_API sstep_status sstep_cg_get_residual(sstep_cg_t handle, double* r_d);
 SSTEP_API sstep_status sstep_cg_lanczos(sstep_cg_t handle, int k, uint64_t seed, double* alpha_h, double* beta_h,
                               int* steps_done);
 
+/* --- allocation-free variant ---------------------------------------------------------- */
+
+/* The Gram reduction, column scaling and FGS (or Cholesky) solve of one outer iteration -
+ * the same kernel and results as sstep_cg_gram_solve - for callers that cannot allocate
+ * device memory, e.g. because a caching allocator already owns the device's memory or
+ * because cudaMalloc/cudaFree would synchronise the device inside a latency-bound loop. It
+ * needs no handle and allocates nothing: its scratch (per-block partial sums and a control
+ * block, about 224 KB) is a static array inside the library, which every GPU that loads the
+ * library holds until the process exits. The paper has no counterpart; it is a calling
+ * convention of this library.
+ *
+ * Inputs: P_d, the basis [p_0 .. p_s] (column-major double, leading dimension ldp >= n,
+ * p_0 = r_k, built as in sstep_cg_basis); mdiag_d, the diagonal of the preconditioner M
+ * (double[n]) or NULL for M = mconst * I (mconst > 0); lambda_min < lambda_max, the bounds the
+ * basis was built with; nu sweeps; gram_solver SSTEP_GRAM_SOLVE_FGS or _CHOLESKY.
+ * Output out_d (device, double[3s + s*s + 1]): alpha = S a (s), d (s), c~ (s), G~ (s*s,
+ * row-major), then the termination state (0 = solved, 3 = numerical breakdown).
+ * Limit: 1 <= s <= 16 (SSTEP_ERR_INVALID_ARG beyond, with the reason in
+ * sstep_cg_last_error(NULL)). Asynchronous on `stream`.
+ * The first call on a device looks up the device address of the static scratch
+ * (cudaGetSymbolAddress with that device current); make it before any stream capture.
+ * All calls on a device share the scratch and it keeps the last call's contents (each call
+ * re-initialises what must start at zero): calls whose work can overlap on the GPU, such as
+ * calls on two streams, race - serialise them. */
+SSTEP_API sstep_status sstep_gram_fgs_noalloc(int64_t n, int s, int nu, int gram_solver, const double* P_d,
+                                              int64_t ldp, const double* mdiag_d, double mconst,
+                                              double lambda_min, double lambda_max, double* out_d, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

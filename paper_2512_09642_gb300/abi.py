@@ -80,6 +80,7 @@ _SIGS = {
     "sstep_cg_get_residual": (_I, [_VP, _VP]),
     "sstep_cg_lanczos": (_I, [_VP, _I, C.c_uint64, _VP, _VP, C.POINTER(_I)]),
     "sstep_cg_grad_kappa": (_I, [_VP, _VP, _VP, _VP]),
+    "sstep_gram_fgs_noalloc": (_I, [_I64, _I, _I, _I, _VP, _I64, _VP, _D, _D, _D, _VP, _VP]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -220,6 +221,16 @@ def sstep_cg_lanczos(h, k: int, seed: int):
 
 def sstep_cg_grad_kappa(h, x, lam, g):
     return _check(lib.sstep_cg_grad_kappa(h, _ptr(x), _ptr(lam), _ptr(g)), h)
+
+
+def sstep_gram_fgs_noalloc(n, s, nu, gram_solver, P, ldp, mdiag, mconst, lambda_min, lambda_max, out,
+                           stream=None):
+    """Allocation-free Gram + FGS (see the header); out: CUDA double tensor of 3s + s*s + 1."""
+    if isinstance(gram_solver, str):
+        gram_solver = GRAM_SOLVER[gram_solver]
+    st = lib.sstep_gram_fgs_noalloc(int(n), int(s), int(nu), int(gram_solver), _ptr(P), int(ldp), _ptr(mdiag),
+                                    float(mconst), float(lambda_min), float(lambda_max), _ptr(out), _stream(stream))
+    return _check(st, None)
 
 
 def exported_names():
