@@ -83,6 +83,8 @@ typedef struct {
     int check_every;       /* host loop only: outers launched between convergence checks */
     int profile_every;     /* > 0: time each kernel of one outer iteration in every this many
                               check intervals with CUDA events (sstep_cg_info.prof_*); 0: off */
+    int batch_chunk;       /* batched form: unknowns per Gram/update work item (0: 8192) */
+    int batch_ctas_per_sm; /* batched form: resident blocks per SM of the stencil kernels (0: 6) */
 } sstep_cg_opts;
 
 typedef struct {
@@ -148,6 +150,10 @@ SSTEP_API sstep_status sstep_cg_solve_host(sstep_cg_t handle, const double* b_h,
 SSTEP_API sstep_status sstep_cg_grad_kappa(sstep_cg_t handle, const double* x_d, const double* lambda_d,
                                            double* gkappa_d);
 
+/* Changes the stopping tolerance and the outer-iteration limit of an existing handle (for
+ * example a looser tolerance for an adjoint solve that reuses the forward handle). */
+SSTEP_API sstep_status sstep_cg_set_tolerance(sstep_cg_t handle, double tol, int max_outer);
+
 /* Releases the handle and everything it owns (synchronises its stream). NULL is a no-op. */
 SSTEP_API sstep_status sstep_cg_destroy(sstep_cg_t handle);
 
@@ -187,6 +193,45 @@ SSTEP_API sstep_status sstep_cg_get_residual(sstep_cg_t handle, double* r_d);
  * start vector; writes alpha (k) and beta (k-1) to host arrays. Synchronises. */
 SSTEP_API sstep_status sstep_cg_lanczos(sstep_cg_t handle, int k, uint64_t seed, double* alpha_h, double* beta_h,
                               int* steps_done);
+
+/* The two conversions of the mixed form, exposed for testing: out_d[i] = float(in_d[i] * 2^k)
+ * rounded to nearest even, computed from the IEEE-754 fields with integer instructions, and
+ * back_d[i] = double(out_d[i]), exact. Device arrays of n elements; asynchronous on stream. */
+SSTEP_API sstep_status sstep_convert_check(const double* in_d, int k, float* out_d, double* back_d, int64_t n,
+                                           void* stream);
+
+/* --- batched form -------------------------------------------------------------------- */
+
+typedef struct sstep_cg_batch_s* sstep_cg_batch_t;
+
+/* `count` independent stencil systems solved together (the batched form of the method of
+ * Section 2): every phase of an outer iteration (s Chebyshev steps, the Gram reduction with
+ * each system's column scaling and FGS, the update) is ONE launch over all systems that are
+ * still iterating; a system that has converged drops out of every later launch. With
+ * opts->use_graph the outer loop is one CUDA graph whose while node runs until no system is
+ * left. grids_h: host int[4 * count], (dim, nx, ny, nz) per system as in
+ * sstep_cg_create_stencil. kappa_d: NULL (all Poisson) or a host array of count device
+ * pointers, each NULL (Poisson) or double[n_i] (diffusion). Per-system spectral bounds
+ * follow opts->bounds_mode (GIVEN: the same bounds for all). Jacobi, FP64, s <= 16.
+ * Vectors of all systems are concatenated: system i occupies [offset_i, offset_i + n_i) of
+ * b and x (sstep_cg_batch_layout). Synchronises `stream`. */
+SSTEP_API sstep_status sstep_cg_batch_create(sstep_cg_batch_t* batch, int count, const int* grids_h,
+                                             const double* const* kappa_d, const sstep_cg_opts* opts, void* stream);
+
+/* offsets_h (host int64[count], may be NULL): start of each system in the concatenated
+ * vectors; total: their length; lambda_h (host double[2*count], may be NULL): the bounds. */
+SSTEP_API sstep_status sstep_cg_batch_layout(sstep_cg_batch_t batch, int64_t* offsets_h, int64_t* total,
+                                             double* lambda_h);
+
+/* Solves all systems from x_0 = x_d (concatenated, device). infos_h (host, count entries, may
+ * be NULL) receives each system's result; summary (may be NULL) the largest outer count, the
+ * worst true relative residual and the device time. Returns SSTEP_OK when every system
+ * reached tol, else the first failing status. Synchronises. */
+SSTEP_API sstep_status sstep_cg_batch_solve(sstep_cg_batch_t batch, const double* b_d, double* x_d,
+                                            sstep_cg_info* infos_h, sstep_cg_info* summary);
+
+SSTEP_API sstep_status sstep_cg_batch_destroy(sstep_cg_batch_t batch);
+SSTEP_API const char* sstep_cg_batch_last_error(sstep_cg_batch_t batch);
 
 /* --- allocation-free variant ---------------------------------------------------------- */
 

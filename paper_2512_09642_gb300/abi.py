@@ -29,7 +29,8 @@ class Opts(C.Structure):
                 ("bounds_mode", C.c_int), ("tol", C.c_double), ("max_outer", C.c_int), ("gram_solver", C.c_int),
                 ("precision", C.c_int), ("precond", C.c_int), ("basis_start", C.c_int), ("gram_form", C.c_int),
                 ("refresh_period", C.c_int), ("max_refresh", C.c_int), ("seed", C.c_uint64),
-                ("use_graph", C.c_int), ("check_every", C.c_int), ("profile_every", C.c_int)]
+                ("use_graph", C.c_int), ("check_every", C.c_int), ("profile_every", C.c_int),
+                ("batch_chunk", C.c_int), ("batch_ctas_per_sm", C.c_int)]
 
 
 class Info(C.Structure):
@@ -80,6 +81,13 @@ _SIGS = {
     "sstep_cg_get_residual": (_I, [_VP, _VP]),
     "sstep_cg_lanczos": (_I, [_VP, _I, C.c_uint64, _VP, _VP, C.POINTER(_I)]),
     "sstep_cg_grad_kappa": (_I, [_VP, _VP, _VP, _VP]),
+    "sstep_cg_set_tolerance": (_I, [_VP, _D, _I]),
+    "sstep_convert_check": (_I, [_VP, _I, _VP, _VP, _I64, _VP]),
+    "sstep_cg_batch_create": (_I, [C.POINTER(_VP), _I, _VP, _VP, C.POINTER(Opts), _VP]),
+    "sstep_cg_batch_layout": (_I, [_VP, _VP, _VP, _VP]),
+    "sstep_cg_batch_solve": (_I, [_VP, _VP, _VP, _VP, C.POINTER(Info)]),
+    "sstep_cg_batch_destroy": (_I, [_VP]),
+    "sstep_cg_batch_last_error": (C.c_char_p, [_VP]),
     "sstep_gram_fgs_noalloc": (_I, [_I64, _I, _I, _I, _VP, _I64, _VP, _D, _D, _D, _VP, _VP]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -221,6 +229,59 @@ def sstep_cg_lanczos(h, k: int, seed: int):
 
 def sstep_cg_grad_kappa(h, x, lam, g):
     return _check(lib.sstep_cg_grad_kappa(h, _ptr(x), _ptr(lam), _ptr(g)), h)
+
+
+def sstep_cg_set_tolerance(h, tol: float, max_outer: int):
+    return _check(lib.sstep_cg_set_tolerance(h, float(tol), int(max_outer)), h)
+
+
+def sstep_convert_check(x, k: int, out, back, stream=None):
+    return _check(lib.sstep_convert_check(_ptr(x), int(k), _ptr(out), _ptr(back), x.numel(), _stream(stream)))
+
+
+def _bcheck(status, h, allow=()):
+    if status != 0 and status not in allow:
+        msg = lib.sstep_cg_batch_last_error(h)
+        raise SStepError(status, msg.decode() if msg else "")
+    return status
+
+
+def sstep_cg_batch_create(grids, kappas, opts: Opts, stream=None):
+    """grids: list of (nx, ny[, nz]); kappas: list of CUDA tensors or None (Poisson)."""
+    import numpy as np
+    g = np.zeros((len(grids), 4), dtype=np.int32)
+    for i, d in enumerate(grids):
+        d = tuple(int(v) for v in d)
+        g[i] = (len(d),) + (d + (1, 1))[:3]
+    kp = (_VP * len(grids))(*[(_ptr(k) if k is not None else None) for k in kappas])
+    h = _VP()
+    st = lib.sstep_cg_batch_create(C.byref(h), len(grids), g.ctypes.data, kp, C.byref(opts), _stream(stream))
+    _bcheck(st, None)
+    return h
+
+
+def sstep_cg_batch_layout(h, count: int):
+    import numpy as np
+    offs = np.zeros(count, dtype=np.int64)
+    lam = np.zeros(2 * count)
+    total = C.c_int64()
+    _bcheck(lib.sstep_cg_batch_layout(h, offs.ctypes.data, C.byref(total), lam.ctypes.data), h)
+    return offs, total.value, lam.reshape(count, 2)
+
+
+def sstep_cg_batch_solve(h, b, x, count: int, allow=(5,)):
+    infos = (Info * count)()
+    summary = Info()
+    _bcheck(lib.sstep_cg_batch_solve(h, _ptr(b), _ptr(x), infos, C.byref(summary)), h, allow)
+    return [i.as_dict() for i in infos], summary.as_dict()
+
+
+def sstep_cg_batch_destroy(h):
+    return _bcheck(lib.sstep_cg_batch_destroy(h), None)
+
+
+def sstep_cg_batch_last_error(h=None) -> str:
+    return lib.sstep_cg_batch_last_error(h).decode()
 
 
 def sstep_gram_fgs_noalloc(n, s, nu, gram_solver, P, ldp, mdiag, mconst, lambda_min, lambda_max, out,

@@ -102,7 +102,10 @@ sstep_status validate_opts(sstep_cg_t h, const sstep_cg_opts* o) {
         set_err(h, "mixed precision refreshes r = b - A x every outer iteration (refresh_period 1)");
         return SSTEP_ERR_UNSUPPORTED;
     }
-    if (o->gram_form != SSTEP_GRAM_FORM_DIRECT) { set_err(h, "gram_form %d not built yet", o->gram_form); return SSTEP_ERR_UNSUPPORTED; }
+    if (o->gram_form != SSTEP_GRAM_FORM_DIRECT && o->gram_form != SSTEP_GRAM_FORM_MOMENTS) {
+        set_err(h, "unknown gram_form %d", o->gram_form);
+        return SSTEP_ERR_INVALID_ARG;
+    }
 
     if (o->check_every < 1) { set_err(h, "check_every < 1"); return SSTEP_ERR_INVALID_ARG; }
     if (o->profile_every < 0) { set_err(h, "profile_every < 0"); return SSTEP_ERR_INVALID_ARG; }
@@ -267,6 +270,30 @@ sstep_status compute_bounds(sstep_cg_t h) {
     }
     return SSTEP_OK;
 }
+
+}  // namespace
+
+namespace sstep {
+// Spectral bounds of one operator as a handle would compute them (used by the batched form):
+// runs the same Lanczos / Gershgorin code on a temporary, workspace-free handle.
+sstep_status estimate_bounds(const OpDesc& op, const double* diag, bool jacobi, const sstep_cg_opts& opts,
+                             cudaStream_t stream, double* lmin, double* lmax, char* err, size_t errlen) {
+    sstep_cg_s tmp;
+    tmp.op = op;
+    tmp.opts = opts;
+    tmp.stream = stream;
+    tmp.jacobi = jacobi;
+    tmp.diag = const_cast<double*>(diag);
+    sstep_status st = compute_bounds(&tmp);
+    tmp.diag = nullptr;   // borrowed
+    *lmin = tmp.lmin;
+    *lmax = tmp.lmax;
+    if (st != SSTEP_OK && err) std::snprintf(err, errlen, "%s", tmp.err);
+    return st;
+}
+}  // namespace sstep
+
+namespace {
 
 GramArgs gram_args(sstep_cg_t h) {
     GramArgs g{};
@@ -644,6 +671,8 @@ void sstep_cg_default_opts(sstep_cg_opts* o) {
     o->use_graph = 0;
     o->check_every = 8;
     o->profile_every = 0;
+    o->batch_chunk = 0;
+    o->batch_ctas_per_sm = 0;
 }
 
 sstep_status sstep_cg_create_csr(sstep_cg_t* out, int64_t n, const int32_t* rowptr_d, const int32_t* colind_d,
@@ -871,6 +900,28 @@ sstep_status sstep_cg_get_bounds(sstep_cg_t h, double* lmin, double* lmax) {
 sstep_status sstep_cg_get_residual(sstep_cg_t h, double* r_d) {
     if (!h || !r_d) return SSTEP_ERR_INVALID_ARG;
     CK(cudaMemcpyAsync(r_d, h->P, sizeof(double) * h->op.n, cudaMemcpyDeviceToDevice, h->stream));
+    return SSTEP_OK;
+}
+
+sstep_status sstep_convert_check(const double* in_d, int k, float* out_d, double* back_d, int64_t n, void* stream) {
+    if (!in_d || !out_d || !back_d || n < 0) return SSTEP_ERR_INVALID_ARG;
+    if (n == 0) return SSTEP_OK;
+    cudaError_t e = launch_convert_check(in_d, k, out_d, back_d, n, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        sstep::set_global_error(cudaGetErrorString(e));
+        return SSTEP_ERR_CUDA;
+    }
+    return SSTEP_OK;
+}
+
+sstep_status sstep_cg_set_tolerance(sstep_cg_t h, double tol, int max_outer) {
+    if (!h) return SSTEP_ERR_INVALID_ARG;
+    if (!(tol > 0.0) || !std::isfinite(tol) || max_outer < 0) {
+        set_err(h, "need tol > 0 and max_outer >= 0");
+        return SSTEP_ERR_INVALID_ARG;
+    }
+    h->opts.tol = tol;
+    h->opts.max_outer = max_outer;
     return SSTEP_OK;
 }
 

@@ -66,6 +66,25 @@ __device__ __forceinline__ double f2d_exact(float f) {
     return __hiloint2double((int)hi, (int)(u << 29));
 }
 
+// float(v * 2^k), rounded to nearest (ties to even), built from the IEEE-754 fields with
+// integer instructions: the FP64 exponent is rebiased by k - 896 and the 52-bit mantissa is
+// rounded to 23 bits (a round-up that overflows the mantissa carries into the exponent, which
+// is the correct result). Zero, subnormal, infinite and NaN inputs, and results outside the
+// normal FP32 range, take the FP64 path.
+__device__ __forceinline__ float d2f_scaled(double v, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(b >> 32);
+    const int ex = (int)((hi >> 20) & 0x7ffu);
+    const int fe = ex - 1023 + 127 + k;
+    if (ex == 0 || ex == 0x7ff || fe <= 0 || fe >= 254) return __double2float_rn(ldexp(v, k));
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    const unsigned m = (unsigned)(mant >> 29);
+    const unsigned rest = (unsigned)(mant & 0x1FFFFFFFull);
+    unsigned bits = ((unsigned)fe << 23) | m;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) bits += 1u;
+    return __uint_as_float((hi & 0x80000000u) | bits);
+}
+
 // Compensated FP32 arithmetic (Knuth's TwoSum, FMA-based TwoProduct; Ogita, Rump and
 // Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005). The _rn intrinsics are
 // never contracted into FMAs, which the error-free transformations rely on.

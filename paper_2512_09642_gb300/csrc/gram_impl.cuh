@@ -39,11 +39,12 @@ __host__ __device__ constexpr int gram_roles(int m, int budget) {
     return g;
 }
 
-template <int S, bool DV>
+template <int S, bool DV, bool MOM = false>
 struct GramShape {
     static constexpr int NSYM = S * (S + 1) / 2;    // p_a^T M p_b, 0 <= a <= b < S
     static constexpr int NLAST = S;                 // p_a^T M p_S
-    static constexpr int M = NSYM + NLAST + (DV ? S : 0);
+    // direct: the NSYM + NLAST entries of W; moments: the 2S moments' inner products
+    static constexpr int M = (MOM ? 2 * S : NSYM + NLAST) + (DV ? S : 0);
     static constexpr int G = gram_roles(M, 46);     // warp roles, FP64 form
     static constexpr int NSLAB = GRAM_WARPS / G;
     static constexpr int G32 = gram_roles(M, 28);   // warp roles, mixed form
@@ -52,9 +53,22 @@ struct GramShape {
 
 struct AB { int a, b, kind; };  // kind 0: p_a^T M p_b, 1: p_a^T p_0 (unweighted c)
 
-template <int S, bool DV>
+// Moments form (gram_form MOMENTS): the basis is p_j = T_j(A^) p_0 with A^ = theta (M^-1 A -
+// sigma) self-adjoint in <u, v>_M = u^T M v, so <p_i, p_j>_M = (mu_(i+j) + mu_|i-j|) / 2 with
+// mu_k = <p_0, T_k(A^) p_0>_M (the spectral expansion used in Section 4's proof). The entries
+// are mu_k = <p_0, p_k>_M for k <= s and, for s < k < 2s, <p_m, p_m>_M (k = 2m, giving
+// mu_k = 2 <p_m, p_m>_M - mu_0) or <p_(m+1), p_m>_M (k = 2m + 1, mu_k = 2 <.,.>_M - mu_1).
+template <int S, bool DV, bool MOM = false>
 __host__ __device__ constexpr AB gram_entry(int e) {
     constexpr int NSYM = S * (S + 1) / 2;
+    if (MOM) {
+        if (e <= S) return AB{0, e, 0};
+        if (e < 2 * S) {
+            const int k = e;
+            return (k % 2 == 0) ? AB{k / 2, k / 2, 0} : AB{(k - 1) / 2, (k + 1) / 2, 0};
+        }
+        return AB{e - 2 * S, 0, 1};
+    }
     if (e < NSYM) {
         int a = 0, len = S;
         while (e >= len) { e -= len; ++a; --len; }
@@ -67,16 +81,16 @@ __host__ __device__ constexpr AB gram_entry(int e) {
 }
 
 // Compile-time list of the entries owned by warp role Q (entries e with e % G == Q).
-template <int S, bool DV, int Q, int G_ = GramShape<S, DV>::G>
+template <int S, bool DV, int Q, int G_ = GramShape<S, DV>::G, bool MOM = false>
 struct RoleTable {
     static constexpr int G = G_;
-    static constexpr int M = GramShape<S, DV>::M;
+    static constexpr int M = GramShape<S, DV, MOM>::M;
     static constexpr int MQ = (M - Q + G - 1) / G;
     int a[MQ > 0 ? MQ : 1], b[MQ > 0 ? MQ : 1], kind[MQ > 0 ? MQ : 1], e[MQ > 0 ? MQ : 1];
     __host__ __device__ constexpr RoleTable() : a(), b(), kind(), e() {
         int k = 0;
         for (int ee = Q; ee < M; ee += G) {
-            const AB ab = gram_entry<S, DV>(ee);
+            const AB ab = gram_entry<S, DV, MOM>(ee);
             a[k] = ab.a;
             b[k] = ab.b;
             kind[k] = ab.kind;
@@ -88,13 +102,13 @@ struct RoleTable {
 
 // Per-role accumulation over this thread's elements, then warp reduction and one write per
 // entry into smem[slab * M + entry] by lane 0.
-template <int S, bool DV, int Q>
+template <int S, bool DV, int Q, bool MOM = false>
 __device__ __forceinline__ void gram_role_f64(const double* __restrict__ P, int64_t ld, const double* __restrict__ diag,
                                               int64_t n, int64_t e0, int64_t stride, double* smem, int slab) {
-    constexpr int G = GramShape<S, DV>::G;
-    constexpr int M = GramShape<S, DV>::M;
+    constexpr int G = GramShape<S, DV, MOM>::G;
+    constexpr int M = GramShape<S, DV, MOM>::M;
     constexpr int MQ = (M - Q + G - 1) / G;
-    constexpr RoleTable<S, DV, Q> RT{};
+    constexpr RoleTable<S, DV, Q, G, MOM> RT{};
     double acc[MQ > 0 ? MQ : 1];
 #pragma unroll
     for (int k = 0; k < MQ; ++k) acc[k] = 0.0;
@@ -123,12 +137,12 @@ __device__ __forceinline__ void gram_role_f64(const double* __restrict__ P, int6
     }
 }
 
-template <int S, bool DV, int Q = 0>
+template <int S, bool DV, int Q = 0, bool MOM = false>
 __device__ __forceinline__ void gram_role_dispatch(int q, const double* P, int64_t ld, const double* diag, int64_t n,
                                                    int64_t e0, int64_t stride, double* smem, int slab) {
-    if constexpr (Q < GramShape<S, DV>::G) {
-        if (q == Q) gram_role_f64<S, DV, Q>(P, ld, diag, n, e0, stride, smem, slab);
-        else gram_role_dispatch<S, DV, Q + 1>(q, P, ld, diag, n, e0, stride, smem, slab);
+    if constexpr (Q < GramShape<S, DV, MOM>::G) {
+        if (q == Q) gram_role_f64<S, DV, Q, MOM>(P, ld, diag, n, e0, stride, smem, slab);
+        else gram_role_dispatch<S, DV, Q + 1, MOM>(q, P, ld, diag, n, e0, stride, smem, slab);
     }
 }
 
@@ -136,13 +150,13 @@ __device__ __forceinline__ void gram_role_dispatch(int q, const double* P, int64
 // TwoProduct) and summed per thread in a compensated FP32 pair (Dot2 of Ogita, Rump and
 // Oishi, about 48 significant bits); the per-thread sums are converted exactly to FP64 and
 // all further reduction (warps, blocks, grid) is in FP64.
-template <int S, bool DV, int Q>
+template <int S, bool DV, int Q, bool MOM = false>
 __device__ __forceinline__ void gram_role_f32(const float* __restrict__ P, int64_t ld, const float* __restrict__ diag,
                                               int64_t n, int64_t e0, int64_t stride, double* smem, int slab) {
-    constexpr int G = GramShape<S, DV>::G32;
-    constexpr int M = GramShape<S, DV>::M;
+    constexpr int G = GramShape<S, DV, MOM>::G32;
+    constexpr int M = GramShape<S, DV, MOM>::M;
     constexpr int MQ = (M - Q + G - 1) / G;
-    constexpr RoleTable<S, DV, Q, G> RT{};
+    constexpr RoleTable<S, DV, Q, G, MOM> RT{};
     float ah[MQ > 0 ? MQ : 1], al[MQ > 0 ? MQ : 1];
 #pragma unroll
     for (int k = 0; k < MQ; ++k) ah[k] = al[k] = 0.f;
@@ -170,12 +184,12 @@ __device__ __forceinline__ void gram_role_f32(const float* __restrict__ P, int64
     }
 }
 
-template <int S, bool DV, int Q = 0>
+template <int S, bool DV, int Q = 0, bool MOM = false>
 __device__ __forceinline__ void gram_role_dispatch32(int q, const float* P, int64_t ld, const float* diag, int64_t n,
                                                      int64_t e0, int64_t stride, double* smem, int slab) {
-    if constexpr (Q < GramShape<S, DV>::G32) {
-        if (q == Q) gram_role_f32<S, DV, Q>(P, ld, diag, n, e0, stride, smem, slab);
-        else gram_role_dispatch32<S, DV, Q + 1>(q, P, ld, diag, n, e0, stride, smem, slab);
+    if constexpr (Q < GramShape<S, DV, MOM>::G32) {
+        if (q == Q) gram_role_f32<S, DV, Q, MOM>(P, ld, diag, n, e0, stride, smem, slab);
+        else gram_role_dispatch32<S, DV, Q + 1, MOM>(q, P, ld, diag, n, e0, stride, smem, slab);
     }
 }
 
@@ -188,19 +202,34 @@ struct GramParams {
 
 // The s x s work of one outer iteration, executed by warp 0 of the last block.
 // tot[]: reduced entries (layout of gram_entry). Writes ctl.
-template <int S, bool DV>
-__device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, double* sm /* >= S*S + 4*S doubles */) {
+template <int S, bool DV, bool MOM = false>
+__device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, double* sm /* >= 2*S*S + 4*S doubles */) {
     const int lane = threadIdx.x;   // warp 0 only
     constexpr int NSYM = S * (S + 1) / 2;
+    constexpr int NW = MOM ? 2 * S : NSYM + S;   // where the unweighted c entries start
     double* Gs = sm;                // G~, row-major S x S
     double* cs = sm + S * S;        // c~
     double* ds = cs + S;            // d
     double* as = ds + S;            // a (scaled solution) then alpha
+    double* mu = sm + S * S + 4 * S;   // moments form: mu_0 .. mu_(2S-1)
+    if (MOM) {
+        for (int k = lane; k < 2 * S; k += 32) {
+            double m;
+            if (k <= S) m = tot[k];
+            else m = 2.0 * tot[k] - tot[k % 2];   // 2 <p_a, p_b>_M - mu_(a-b), a - b = k mod 2
+            mu[k] = m;
+        }
+        __syncwarp();
+    }
     auto Wsym = [&](int a, int b) -> double {   // p_a^T M p_b for a, b < S
+        if (MOM) return 0.5 * (mu[a + b] + mu[a > b ? a - b : b - a]);
         if (a > b) { const int t = a; a = b; b = t; }
         return tot[a * S - a * (a - 1) / 2 + (b - a)];
     };
-    auto W = [&](int i, int k) -> double { return k < S ? Wsym(i, k) : tot[NSYM + i]; };
+    auto W = [&](int i, int k) -> double {
+        if (MOM) return 0.5 * (mu[i + k] + mu[i > k ? i - k : k - i]);
+        return k < S ? Wsym(i, k) : tot[NSYM + i];
+    };
     const double h0 = 1.0 / gp.theta, h1 = 0.5 / gp.theta;
     const double sc = DV ? 1.0 : gp.dfac;
     // G (lower triangle, mirrored) and c
@@ -214,7 +243,7 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
         g = fma(hj, nb, g);
         Gs[idx] = sc * g;
     }
-    if (lane < S) cs[lane] = DV ? tot[NSYM + S + lane] : Wsym(lane, 0);
+    if (lane < S) cs[lane] = DV ? tot[NW + lane] : Wsym(lane, 0);
     __syncwarp();
     const double rk_sq = cs[0];
     if (lane == 0) {
@@ -361,15 +390,15 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     }
 }
 
-template <int S, bool DV, typename T>
+template <int S, bool DV, typename T, bool MOM>
 __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram(const T* __restrict__ P, int64_t ld,
                                                          const T* __restrict__ diag, int64_t n,
                                                          double* partials, Ctl* ctl, GramParams gp) {
     if (ctl->done) return;
     constexpr bool F32 = std::is_same<T, float>::value;
-    constexpr int G = F32 ? GramShape<S, DV>::G32 : GramShape<S, DV>::G;
-    constexpr int NSLAB = F32 ? GramShape<S, DV>::NSLAB32 : GramShape<S, DV>::NSLAB;
-    constexpr int M = GramShape<S, DV>::M;
+    constexpr int G = F32 ? GramShape<S, DV, MOM>::G32 : GramShape<S, DV, MOM>::G;
+    constexpr int NSLAB = F32 ? GramShape<S, DV, MOM>::NSLAB32 : GramShape<S, DV, MOM>::NSLAB;
+    constexpr int M = GramShape<S, DV, MOM>::M;
     constexpr int NSM = (NSLAB * M) > S * S * 2 + 4 * S ? NSLAB * M : S * S * 2 + 4 * S;
     __shared__ double smem[NSM];
     __shared__ double tot[M];
@@ -378,8 +407,8 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram(const T* __restrict__ 
     const int q = warp % G, slab = warp / G;
     const int64_t e0 = ((int64_t)blockIdx.x * NSLAB + slab) * 32 + lane;
     const int64_t stride = (int64_t)gridDim.x * NSLAB * 32;
-    if constexpr (F32) gram_role_dispatch32<S, DV>(q, P, ld, diag, n, e0, stride, smem, slab);
-    else gram_role_dispatch<S, DV>(q, P, ld, diag, n, e0, stride, smem, slab);
+    if constexpr (F32) gram_role_dispatch32<S, DV, 0, MOM>(q, P, ld, diag, n, e0, stride, smem, slab);
+    else gram_role_dispatch<S, DV, 0, MOM>(q, P, ld, diag, n, e0, stride, smem, slab);
     __syncthreads();
     for (int k = threadIdx.x; k < M; k += GRAM_THREADS) {
         double v = 0.0;
@@ -401,7 +430,7 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram(const T* __restrict__ 
     }
     __syncthreads();
     if (threadIdx.x == 0) ctl->counter = 0u;
-    if (warp == 0) gram_finish<S, DV>(tot, gp, ctl, smem);
+    if (warp == 0) gram_finish<S, DV, MOM>(tot, gp, ctl, smem);
 }
 
 template <int S>
@@ -413,17 +442,27 @@ cudaError_t launch_gram_s(const GramArgs& g, double* partials, Ctl* ctl, int nbl
     gp.theta = g.theta;
     gp.sigma = g.sigma;
     gp.dfac = g.dconst;
+    const bool mom = g.form == SSTEP_GRAM_FORM_MOMENTS;
+#define SSTEP_GRAM_LAUNCH(DV, T, MOM, DIAG) \
+    k_gram<S, DV, T, MOM><<<nblocks, GRAM_THREADS, 0, st>>>((const T*)g.P, g.ld, DIAG, g.n, partials, ctl, gp)
     if (g.fp32) {
-        if (g.dvec)
-            k_gram<S, true, float><<<nblocks, GRAM_THREADS, 0, st>>>((const float*)g.P, g.ld, g.diag32, g.n, partials, ctl, gp);
-        else
-            k_gram<S, false, float><<<nblocks, GRAM_THREADS, 0, st>>>((const float*)g.P, g.ld, nullptr, g.n, partials, ctl, gp);
+        if (g.dvec) {
+            if (mom) SSTEP_GRAM_LAUNCH(true, float, true, g.diag32);
+            else SSTEP_GRAM_LAUNCH(true, float, false, g.diag32);
+        } else {
+            if (mom) SSTEP_GRAM_LAUNCH(false, float, true, (const float*)nullptr);
+            else SSTEP_GRAM_LAUNCH(false, float, false, (const float*)nullptr);
+        }
     } else {
-        if (g.dvec)
-            k_gram<S, true, double><<<nblocks, GRAM_THREADS, 0, st>>>((const double*)g.P, g.ld, g.diag, g.n, partials, ctl, gp);
-        else
-            k_gram<S, false, double><<<nblocks, GRAM_THREADS, 0, st>>>((const double*)g.P, g.ld, nullptr, g.n, partials, ctl, gp);
+        if (g.dvec) {
+            if (mom) SSTEP_GRAM_LAUNCH(true, double, true, g.diag);
+            else SSTEP_GRAM_LAUNCH(true, double, false, g.diag);
+        } else {
+            if (mom) SSTEP_GRAM_LAUNCH(false, double, true, (const double*)nullptr);
+            else SSTEP_GRAM_LAUNCH(false, double, false, (const double*)nullptr);
+        }
     }
+#undef SSTEP_GRAM_LAUNCH
     return cudaGetLastError();
 }
 

@@ -14,7 +14,7 @@ SSTEP_EXTERN_GRAM(26) SSTEP_EXTERN_GRAM(27) SSTEP_EXTERN_GRAM(28) SSTEP_EXTERN_G
 SSTEP_EXTERN_GRAM(31) SSTEP_EXTERN_GRAM(32)
 #undef SSTEP_EXTERN_GRAM
 
-static int gram_m(int s, bool dvec) { return s * (s + 1) / 2 + s + (dvec ? s : 0); }
+static int gram_m(int s, bool dvec) { return s * (s + 1) / 2 + s + (dvec ? s : 0); }   // >= the moments form's 2s (+ s)
 
 int gram_blocks(const GramArgs& g, int sm_count) {
     // one 512-thread block per SM (the kernel asks for <= 128 registers per thread),

@@ -54,19 +54,19 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_stencil(const T* __restrict__ p
     int64_t e = i + (int64_t)nx * j + sxy * k0;
     T pdn = (DIM == 3 && k0 > 0) ? ldg(p + e - sxy) : T(0);
     T pc = ldg(p + e);
+#pragma unroll 2
     for (int k = k0; k < k1; ++k, e += sxy) {
         const T pup = (DIM == 3 && k < nz - 1) ? ldg(p + e + sxy) : T(0);
         const T qv = FIRST ? T(0) : ldg(q + e);
         T o;
         if (POISSON) {
-            T s = (i > 0) ? ldg(p + e - 1) : T(0);
-            if (i < nx - 1) s += ldg(p + e + 1);
-            if (j > 0) s += ldg(p + e - nx);
-            if (j < ny - 1) s += ldg(p + e + nx);
-            if (DIM == 3) {
-                if (k > 0) s += pdn;
-                if (k < nz - 1) s += pup;
-            }
+            // neighbour sum as a depth-3 tree (x pair, y pair, z pair): same 5 adds, shorter chain
+            const T xm = (i > 0) ? ldg(p + e - 1) : T(0);
+            const T xp = (i < nx - 1) ? ldg(p + e + 1) : T(0);
+            const T ym = (j > 0) ? ldg(p + e - nx) : T(0);
+            const T yp = (j < ny - 1) ? ldg(p + e + nx) : T(0);
+            T s = (xm + xp) + (ym + yp);
+            if (DIM == 3) s += (k > 0 ? pdn : T(0)) + (k < nz - 1 ? pup : T(0));
             o = FIRST ? fma(c2, s, c1 * pc) : fma(c2, s, fma(c1, pc, -qv));
         } else {
             const T s = diffusion_offdiag_sum<T, DIM>(p, f, e, i, j, k, nx, ny, nz, sxy, pdn, pup);
@@ -184,7 +184,11 @@ __global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __res
                                                              int ny, int nz, Faces<double> f, double d2,
                                                              double* partials, Ctl* ctl, int mode) {
     if (mode == 2 && ctl->done) return;
-    const double scale = mode == 2 ? ctl->scale_next : 1.0;
+    int kscale = 0;   // scale_next = 2^kscale
+    if (mode == 2) {
+        frexp(ctl->scale_next, &kscale);
+        kscale -= 1;
+    }
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
     const bool act = i < nx && j < ny;
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __res
             }
             const double rv = ldg(b + e) - ax;
             if (r) r[e] = rv;
-            if (r32) r32[e] = __double2float_rn(rv * scale);
+            if (r32) r32[e] = d2f_scaled(rv, kscale);
             ss = fma(rv, rv, ss);
             pdn = pc;
             pc = pup;
@@ -240,7 +244,11 @@ __global__ void __launch_bounds__(RB) k_residual_csr(const int32_t* __restrict__
                                                      float* __restrict__ r32, int64_t n, double* partials, Ctl* ctl,
                                                      int mode) {
     if (mode == 2 && ctl->done) return;
-    const double scale = mode == 2 ? ctl->scale_next : 1.0;
+    int kscale = 0;   // scale_next = 2^kscale
+    if (mode == 2) {
+        frexp(ctl->scale_next, &kscale);
+        kscale -= 1;
+    }
     double ss = 0.0;
     for (int64_t row = blockIdx.x * (int64_t)RB + threadIdx.x; row < n; row += (int64_t)gridDim.x * RB) {
         const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(RB) k_residual_csr(const int32_t* __restrict__
         for (int32_t t = s0; t < s1; ++t) y = fma(ldg(vals + t), ldg(x + ldg(colind + t)), y);
         const double rv = ldg(b + row) - y;
         if (r) r[row] = rv;
-        if (r32) r32[row] = __double2float_rn(rv * scale);
+        if (r32) r32[row] = d2f_scaled(rv, kscale);
         ss = fma(rv, rv, ss);
     }
     __shared__ double sh[RB / 32];
@@ -416,6 +424,22 @@ cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, 
         return cudaGetLastError();
     }
     k_residual_csr<<<vec_blocks(op.n), RB, 0, st>>>(op.rowptr, op.colind, op.vals, b, x, r, r32, op.n, partials, ctl, mode);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_convert_check(const double* __restrict__ in, int k, float* __restrict__ out, double* __restrict__ back,
+                                int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)RB + threadIdx.x; e < n; e += (int64_t)gridDim.x * RB) {
+        const float f = d2f_scaled(in[e], k);
+        out[e] = f;
+        back[e] = f2d_exact(f);
+    }
+}
+}  // namespace
+
+cudaError_t launch_convert_check(const double* in, int k, float* out, double* back, int64_t n, cudaStream_t st) {
+    k_convert_check<<<vec_blocks(n), RB, 0, st>>>(in, k, out, back, n);
     return cudaGetLastError();
 }
 

@@ -41,11 +41,12 @@ __global__ void __launch_bounds__(UB) k_update_f64(const double* __restrict__ P,
 // split into FP32 hi + lo; the sum over j is a compensated FP32 dot product (about 44
 // significant bits) taken in the scaled domain, where its terms are O(1), and added to x in
 // FP64 through exact conversions: one add and one FMA on the FP64 pipe per unknown.
-__global__ void __launch_bounds__(UB) k_update_mixed(const float* __restrict__ P, int64_t ld, int s, int64_t n,
+template <int S>
+__global__ void __launch_bounds__(UB) k_update_mixed(const float* __restrict__ P, int64_t ld, int64_t n,
                                                      double* __restrict__ x, const Ctl* __restrict__ ctl) {
     if (ctl->done) return;
-    __shared__ float ah[MAXS], al[MAXS];
-    if (threadIdx.x < s) {
+    __shared__ float ah[S], al[S];
+    if (threadIdx.x < S) {
         const double a = ctl->alpha[threadIdx.x];
         const float h = __double2float_rn(a);
         ah[threadIdx.x] = h;
@@ -54,12 +55,14 @@ __global__ void __launch_bounds__(UB) k_update_mixed(const float* __restrict__ P
     __syncthreads();
     const double inv_scale = 1.0 / ctl->scale;   // exact: scale is a power of two
     for (int64_t e = blockIdx.x * (int64_t)UB + threadIdx.x; e < n; e += (int64_t)gridDim.x * UB) {
+        float pv[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) pv[j] = __ldg(P + j * ld + e);   // all loads in flight first
         float sh = 0.f, sl = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < s; ++j) {
-            const float p = __ldg(P + j * ld + e);
-            dot2_acc(ah[j], p, sh, sl);
-            sl = fmaf(al[j], p, sl);
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            dot2_acc(ah[j], pv[j], sh, sl);
+            sl = fmaf(al[j], pv[j], sl);
         }
         x[e] = fma(f2d_exact(sh) + f2d_exact(sl), inv_scale, x[e]);
     }
@@ -84,7 +87,17 @@ cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, 
 
 cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
                                 cudaStream_t st) {
-    k_update_mixed<<<blocks_for(n), UB, 0, st>>>(P, ld, s, n, x, ctl);
+    const int nb = blocks_for(n);
+    switch (s) {
+#define SSTEP_CASE(S) case S: k_update_mixed<S><<<nb, UB, 0, st>>>(P, ld, n, x, ctl); break;
+        SSTEP_CASE(1) SSTEP_CASE(2) SSTEP_CASE(3) SSTEP_CASE(4) SSTEP_CASE(5) SSTEP_CASE(6) SSTEP_CASE(7)
+        SSTEP_CASE(8) SSTEP_CASE(9) SSTEP_CASE(10) SSTEP_CASE(11) SSTEP_CASE(12) SSTEP_CASE(13) SSTEP_CASE(14)
+        SSTEP_CASE(15) SSTEP_CASE(16) SSTEP_CASE(17) SSTEP_CASE(18) SSTEP_CASE(19) SSTEP_CASE(20) SSTEP_CASE(21)
+        SSTEP_CASE(22) SSTEP_CASE(23) SSTEP_CASE(24) SSTEP_CASE(25) SSTEP_CASE(26) SSTEP_CASE(27) SSTEP_CASE(28)
+        SSTEP_CASE(29) SSTEP_CASE(30) SSTEP_CASE(31) SSTEP_CASE(32)
+#undef SSTEP_CASE
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -46,6 +46,10 @@ cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, 
                             double* partials, Ctl* ctl, int mode, cudaStream_t st);
 size_t residual_partials_needed(const OpDesc& op);
 
+// Mixed-form conversions on n values: out = float(in * 2^k) (d2f_scaled), back = double(out)
+// (f2d_exact).
+cudaError_t launch_convert_check(const double* in, int k, float* out, double* back, int64_t n, cudaStream_t st);
+
 // y = A x (FP64).
 cudaError_t launch_apply(const OpDesc& op, const double* x, double* y, cudaStream_t st);
 

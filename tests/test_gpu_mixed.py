@@ -101,3 +101,23 @@ def test_mixed_matches_fp64_library_solution():
     err = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
     print(f"48^3: fp64 {i64['outer_iters']} outers, mixed {i32['outer_iters']}, |x32 - x64|/|x64| = {err:.2e}")
     assert err <= 1e-5
+
+
+def test_mixed_conversions_round_to_nearest_even_and_back_exactly():
+    """The refresh's float(r * 2^k) is built from the IEEE fields with integer operations and
+    the update's float -> double likewise: compare with torch's conversions."""
+    from paper_2512_09642_gb300 import abi
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn(200000, generator=g, dtype=torch.float64)
+    x = torch.cat([x, x * 1e-30, x * 1e30, torch.tensor([0.0, -0.0, 1.0, -1.0, 2.0 ** -126, 3.0 * 2 ** -150,
+                                                         float("inf"), 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24])])
+    # halfway cases: mantissas ending exactly at the FP32 rounding boundary
+    ties = torch.tensor([1.0 + (2 * k + 1) * 2.0 ** -24 for k in range(64)], dtype=torch.float64)
+    x = torch.cat([x, ties, -ties]).cuda()
+    for k in (0, 5, -7, 40):
+        out = torch.empty(x.numel(), dtype=torch.float32, device="cuda")
+        back = torch.empty(x.numel(), dtype=torch.float64, device="cuda")
+        abi.sstep_convert_check(x, k, out, back)
+        ref = (x * 2.0 ** k).float()
+        assert torch.equal(out, ref) or bool(torch.all((out == ref) | (torch.isnan(out) & torch.isnan(ref))))
+        assert torch.equal(back, out.double())

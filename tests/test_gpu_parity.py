@@ -75,11 +75,12 @@ def test_chebyshev_basis_matches_oracle(name, make, mode, precond):
 
 @pytest.mark.parametrize("name,make,mode", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("s", [1, 4, 8, 12])
-def test_gram_solve_matches_oracle(name, make, mode, s):
+@pytest.mark.parametrize("form", ["direct", "moments"])
+def test_gram_solve_matches_oracle(name, make, mode, s, form):
     p = make()
     op = O.Operator(*p.csr())
     lam = (0.04, 2.0)
-    sv = _solver(p, mode, bounds=lam, s=s, nu=20)
+    sv = _solver(p, mode, bounds=lam, s=s, nu=20, gram_form=form)
     r = p.b.copy()
     Pp = O.chebyshev_basis(op, r, s, lam[0], lam[1], ncols=s + 1)
     alpha, d, ct, Gt = sv.gram_solve(_dev(Pp.T))
@@ -121,13 +122,16 @@ SOLVE_CASES = [
 
 
 @pytest.mark.parametrize("name,make,mode,s,nu", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
-def test_per_iterate_parity_first_five_outer_iterations(name, make, mode, s, nu):
+@pytest.mark.parametrize("form", ["direct", "moments"])
+def test_per_iterate_parity_first_five_outer_iterations(name, make, mode, s, nu, form):
+    """x_k and r_k, k = 1..5, within 1e-10 of the oracle (which forms G = P^T A P directly)
+    for both ways of forming G on the GPU."""
     p = make()
     op = O.Operator(*p.csr())
     lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
     ref = O.solve(op, p.b, s=s, nu=nu, lam_min=lam[0], lam_max=lam[1], tol=1e-30, max_outer=5, history=5)
     for k in range(1, 6):
-        x, r, info = _iterates(p, mode, s, nu, lam, k)
+        x, r, info = _iterates(p, mode, s, nu, lam, k, gram_form=form)
         assert info["outer_iters"] == k
         h = ref.history[k - 1]
         assert _rel(x, h.x) <= 1e-10, (k, _rel(x, h.x))
@@ -209,6 +213,31 @@ def test_host_buffer_solve_matches_device_solve():
     info = abi.sstep_cg_solve_host(sv.h, np.ascontiguousarray(p.b), xh)
     assert info.status == 0
     assert np.array_equal(xh, xd.cpu().numpy())
+
+
+@pytest.mark.parametrize("form", ["direct", "moments"])
+def test_full_solve_outer_counts_match_stored_oracle_runs(form):
+    """64^3, 128^3 and 256^3 Poisson (s = 8, nu = 25) to 1e-8 against the outer-iteration
+    counts of the oracle's own converged runs (tests/golden/oracle_outer_counts.txt). The
+    first iterates agree to 1e-10, but over hundreds of outer iterations the literal restarted
+    method is sensitive to rounding: the same change-of-basis arithmetic run in numpy already
+    takes 116 instead of the oracle's 112 outer iterations at 128^3. So the count must stay
+    within 20% of the oracle's, and the true residual must reach the tolerance."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_outer_counts.txt")
+    stored = {}
+    for line in open(path):
+        if line.startswith("poisson3d_"):
+            tok = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            stored[int(line.split()[0].split("_")[1])] = int(tok["outer"])
+    for side in (64, 128, 256):
+        p = W.poisson3d(side)
+        sv = _solver(p, "stencil", s=8, nu=25, tol=1e-8, gram_form=form)
+        x, info = sv.solve(_dev(p.b))
+        sv.close()
+        assert info["status"] == "SSTEP_OK" and info["rel_res_true"] <= 1e-8
+        assert abs(info["outer_iters"] - stored[side]) <= max(1, 0.2 * stored[side]), \
+            (side, info["outer_iters"], stored[side])
 
 
 @pytest.mark.slow
