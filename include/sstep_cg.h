@@ -129,6 +129,18 @@ SSTEP_API sstep_status sstep_cg_create_stencil(sstep_cg_t* handle, int dim, int 
                                      const double* kappa_d, const sstep_cg_opts* opts,
                                      void* stream);
 
+/* Matrix-free handle over the box-stencil Poisson operator on a structured grid with
+ * homogeneous Dirichlet boundaries: every grid point of the unit box around a point (3^dim - 1
+ * of them: faces, edges and corners) is a neighbour with weight -1 and the diagonal is
+ * 3^dim - 1. In 3D this is the 27-point finite-difference Laplacian of the experiments in
+ * Section 8 (unscaled: the h^-2 factor changes neither the Jacobi-preconditioned iteration
+ * nor the relative residual); in 2D the 9-point one. dim = 2 (nz must be 1) or 3. M = D is
+ * the constant 3^dim - 1, so the moments Gram form applies. The Gershgorin bound of D^-1 A
+ * is 2, well above the spectrum's end near 36/26 in 3D; the paper's Lanczos-10 bounds
+ * (bounds_mode LANCZOS10) are tighter. Synchronises `stream`. */
+SSTEP_API sstep_status sstep_cg_create_box_stencil(sstep_cg_t* handle, int dim, int nx, int ny, int nz,
+                                                   const sstep_cg_opts* opts, void* stream);
+
 /* Solves A x = b from the initial guess in x_d (in: x_0, out: x). b_d, x_d: double[n].
  * info may be NULL. Synchronises the handle's stream (it reads the convergence state).
  * Returns SSTEP_OK when ||b - A x|| / ||b - A x_0|| < tol, SSTEP_ERR_NO_CONVERGENCE when
@@ -212,7 +224,8 @@ typedef struct sstep_cg_batch_s* sstep_cg_batch_t;
  * left. grids_h: host int[4 * count], (dim, nx, ny, nz) per system as in
  * sstep_cg_create_stencil. kappa_d: NULL (all Poisson) or a host array of count device
  * pointers, each NULL (Poisson) or double[n_i] (diffusion). Per-system spectral bounds
- * follow opts->bounds_mode (GIVEN: the same bounds for all). Jacobi, FP64, s <= 16.
+ * follow opts->bounds_mode (GIVEN: the same bounds for all). Jacobi, FP64, s <= 16; the
+ * Gram in either opts->gram_form (DIRECT or MOMENTS). Other options give SSTEP_ERR_UNSUPPORTED.
  * Vectors of all systems are concatenated: system i occupies [offset_i, offset_i + n_i) of
  * b and x (sstep_cg_batch_layout). Synchronises `stream`. */
 SSTEP_API sstep_status sstep_cg_batch_create(sstep_cg_batch_t* batch, int count, const int* grids_h,

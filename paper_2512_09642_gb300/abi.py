@@ -68,6 +68,7 @@ _SIGS = {
     "sstep_cg_default_opts": (None, [C.POINTER(Opts)]),
     "sstep_cg_create_csr": (_I, [C.POINTER(_VP), _I64, _VP, _VP, _VP, C.POINTER(Opts), _VP]),
     "sstep_cg_create_stencil": (_I, [C.POINTER(_VP), _I, _I, _I, _I, _VP, C.POINTER(Opts), _VP]),
+    "sstep_cg_create_box_stencil": (_I, [C.POINTER(_VP), _I, _I, _I, _I, C.POINTER(Opts), _VP]),
     "sstep_cg_solve": (_I, [_VP, _VP, _VP, C.POINTER(Info)]),
     "sstep_cg_solve_host": (_I, [_VP, _VP, _VP, C.POINTER(Info)]),
     "sstep_cg_destroy": (_I, [_VP]),
@@ -156,6 +157,14 @@ def sstep_cg_create_stencil(dim: int, nx: int, ny: int, nz: int, kappa, opts: Op
     h = _VP()
     st = lib.sstep_cg_create_stencil(C.byref(h), int(dim), int(nx), int(ny), int(nz), _ptr(kappa), C.byref(opts),
                                      _stream(stream))
+    _check(st, None)
+    return h
+
+
+def sstep_cg_create_box_stencil(dim: int, nx: int, ny: int, nz: int, opts: Opts, stream=None):
+    h = _VP()
+    st = lib.sstep_cg_create_box_stencil(C.byref(h), int(dim), int(nx), int(ny), int(nz), C.byref(opts),
+                                         _stream(stream))
     _check(st, None)
     return h
 

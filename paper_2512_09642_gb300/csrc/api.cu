@@ -221,6 +221,15 @@ sstep_status lanczos(sstep_cg_t h, int k, uint64_t seed, std::vector<double>& al
 }
 
 sstep_status gershgorin(sstep_cg_t h, double* out) {
+    if (h->op.kind == OP_STENCIL && h->op.box) {
+        // box stencil: row sum of |a_ij| = (3^dim - 1) + (in-grid box neighbours), maximal in
+        // the interior, where every extent contributes min(3, n_axis) points
+        const int D = h->op.dim == 3 ? 26 : 8;
+        int pts = (h->op.nx < 3 ? h->op.nx : 3) * (h->op.ny < 3 ? h->op.ny : 3);
+        if (h->op.dim == 3) pts *= (h->op.nz < 3 ? h->op.nz : 3);
+        *out = h->jacobi ? (double)(D + pts - 1) / D : (double)(D + pts - 1);
+        return SSTEP_OK;
+    }
     if (h->op.kind == OP_STENCIL && h->op.wx == nullptr) {
         // Poisson: row sum of |a_ij| = 2 dim + (in-grid neighbours); maximal in the interior
         const int d2 = 2 * h->op.dim;
@@ -751,6 +760,31 @@ sstep_status sstep_cg_create_stencil(sstep_cg_t* out, int dim, int nx, int ny, i
         if (hb) { set_err(h, "kappa must be positive and finite"); return fail_create(h, SSTEP_ERR_INVALID_ARG); }
         h->kappa = kappa_d;
     }
+    st = finish_create(h);
+    if (st != SSTEP_OK) return fail_create(h, st);
+    *out = h;
+    return SSTEP_OK;
+}
+
+sstep_status sstep_cg_create_box_stencil(sstep_cg_t* out, int dim, int nx, int ny, int nz, const sstep_cg_opts* opts,
+                                         void* stream) {
+    sstep_cg_t h = nullptr;
+    sstep_status st = begin_create(out, opts, stream, &h);
+    if (st != SSTEP_OK) return fail_create(h, st);
+    if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || nz < 1 || (dim == 2 && nz != 1) || ny > 65535 * 8 ||
+        (dim == 3 && nz > 65535 * 16)) {
+        set_err(h, "bad grid: dim %d, %d x %d x %d", dim, nx, ny, nz);
+        return fail_create(h, SSTEP_ERR_INVALID_ARG);
+    }
+    if ((st = bind_device(h)) != SSTEP_OK) return fail_create(h, st);
+    h->op.kind = OP_STENCIL;
+    h->op.box = 1;
+    h->op.n = (int64_t)nx * ny * nz;
+    h->op.dim = dim;
+    h->op.nx = nx;
+    h->op.ny = ny;
+    h->op.nz = nz;
+    h->op.dconst = dim == 3 ? 26.0 : 8.0;
     st = finish_create(h);
     if (st != SSTEP_OK) return fail_create(h, st);
     *out = h;

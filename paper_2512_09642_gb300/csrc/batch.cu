@@ -40,6 +40,7 @@ struct sstep_cg_batch_s {
     Ctl* ctl_h = nullptr;
     int* running = nullptr;
     int* running_h = nullptr;
+    int* act = nullptr;          // act_sys | act_tile_prefix | act_chunk_prefix | act_n
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -86,18 +87,24 @@ BatchDev dev_view(sstep_cg_batch_t h) {
     B.gram_partials = h->gram_partials;
     B.tile_partials = h->tile_partials;
     B.ctas_per_sm = h->opts.batch_ctas_per_sm > 0 ? h->opts.batch_ctas_per_sm : 6;
+    B.act_sys = h->act;
+    B.act_tile_prefix = h->act + h->count;
+    B.act_chunk_prefix = h->act + 2 * h->count + 1;
+    B.act_n = h->act + 3 * h->count + 2;
     return B;
 }
 
 sstep_status batch_outer(sstep_cg_batch_t h, cudaStream_t st) {
     const BatchDev B = dev_view(h);
     const int s = h->opts.s;
+    BCK(launch_batch_compact(B, st));
     for (int j = 0; j < s; ++j) {
         const double* p = h->P + (int64_t)j * h->ld;
         const double* q = j > 0 ? h->P + (int64_t)(j - 1) * h->ld : h->P;
         BCK(launch_batch_cheb(B, p, q, h->P + (int64_t)(j + 1) * h->ld, j == 0, st));
     }
-    BCK(launch_batch_gram(B, s, h->opts.nu, h->opts.gram_solver, h->P, st));
+    BCK(launch_batch_gram(B, s, h->opts.nu, h->opts.gram_solver, h->opts.gram_form == SSTEP_GRAM_FORM_MOMENTS, h->P,
+                          st));
     return SSTEP_OK;
 }
 
@@ -171,9 +178,9 @@ sstep_status sstep_cg_batch_create(sstep_cg_batch_t* out, int count, const int* 
         berr(h, "unknown gram_solver");
         return fail(SSTEP_ERR_INVALID_ARG);
     }
-    if (o.precond != SSTEP_PRECOND_JACOBI || o.precision != SSTEP_PRECISION_FP64 ||
-        o.gram_form != SSTEP_GRAM_FORM_DIRECT || o.basis_start != SSTEP_START_R) {
-        berr(h, "batched form: Jacobi, FP64, direct Gram and p_0 = r only");
+    if (o.precond != SSTEP_PRECOND_JACOBI || o.precision != SSTEP_PRECISION_FP64 || o.basis_start != SSTEP_START_R ||
+        (o.gram_form != SSTEP_GRAM_FORM_DIRECT && o.gram_form != SSTEP_GRAM_FORM_MOMENTS)) {
+        berr(h, "batched form: Jacobi, FP64 and p_0 = r only");
         return fail(SSTEP_ERR_UNSUPPORTED);
     }
     if (o.bounds_mode == SSTEP_BOUNDS_GIVEN && !(o.lambda_max > o.lambda_min && o.lambda_min >= 0.0)) {
@@ -207,8 +214,9 @@ sstep_status sstep_cg_batch_create(sstep_cg_batch_t* out, int count, const int* 
         sy.poisson = (kappa_d == nullptr || kappa_d[i] == nullptr) ? 1 : 0;
         off += (sy.n + 31) / 32 * 32;
         sy.tile0 = (int)h->tiles.size();
+        // 3D tile: 32 x 8 points x 8 planes; 2D tile: 32 x 64 points (8 row groups of 8)
         for (int k0 = 0; k0 < nz; k0 += (dim == 3 ? BT_Z : 1))
-            for (int j0 = 0; j0 < ny; j0 += BT_Y)
+            for (int j0 = 0; j0 < ny; j0 += (dim == 3 ? BT_Y : BT_Y * BT_Z))
                 for (int i0 = 0; i0 < nx; i0 += BT_X) h->tiles.push_back(BTile{i, i0, j0, k0});
         sy.tile1 = (int)h->tiles.size();
         sy.chunk0 = (int)h->chunks.size();
@@ -229,7 +237,8 @@ sstep_status sstep_cg_batch_create(sstep_cg_batch_t* out, int count, const int* 
         cudaMallocHost(&h->running_h, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&h->sys_d, sizeof(BSys) * count) != cudaSuccess ||
         cudaMalloc(&h->tiles_d, sizeof(BTile) * h->tiles.size()) != cudaSuccess ||
-        cudaMalloc(&h->chunks_d, sizeof(BChunk) * h->chunks.size()) != cudaSuccess) {
+        cudaMalloc(&h->chunks_d, sizeof(BChunk) * h->chunks.size()) != cudaSuccess ||
+        cudaMalloc(&h->act, sizeof(int) * (3 * count + 5)) != cudaSuccess) {
         berr(h, "batched form: out of device memory (%lld unknowns)", (long long)ld);
         return fail(SSTEP_ERR_OOM);
     }
@@ -332,7 +341,7 @@ sstep_status sstep_cg_batch_solve(sstep_cg_batch_t h, const double* b_d, double*
     BCK(launch_batch_residual(B, b_d, x_d, h->P, 0, st));
     std::vector<int> refreshes(count, 0);
     long launches = 2;
-    const int per_outer = h->opts.s + 2;
+    const int per_outer = h->opts.s + 3;
     for (;;) {
         if (h->opts.use_graph) {
             if (!h->gexec || h->g_b != b_d || h->g_x != x_d) {
@@ -439,6 +448,7 @@ sstep_status sstep_cg_batch_destroy(sstep_cg_batch_t h) {
     cudaFree(h->sys_d);
     cudaFree(h->tiles_d);
     cudaFree(h->chunks_d);
+    cudaFree(h->act);
     if (h->ctl_h) cudaFreeHost(h->ctl_h);
     if (h->running_h) cudaFreeHost(h->running_h);
     delete h;

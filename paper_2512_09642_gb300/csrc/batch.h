@@ -38,16 +38,41 @@ struct BatchDev {
     double* gram_partials; // [nchunks][M]
     double* tile_partials; // [ntiles]
     int ctas_per_sm;       // grid of the stencil kernels: ctas_per_sm x SMs (capped by the tiles)
+    // active work of the current outer iteration (k_batch_compact): running systems and the
+    // prefix sums of their tile and chunk counts; act_n = {systems, tiles, chunks}
+    int* act_sys;
+    int* act_tile_prefix;
+    int* act_chunk_prefix;
+    int* act_n;
 };
+
+// Locates active work item t: returns the index into act_sys whose prefix range holds t,
+// starting the forward scan at `hint` (items are visited in increasing order by a block).
+__device__ __forceinline__ int batch_find(const int* prefix, int nact, int t, int hint) {
+    int lo = hint;
+    if (lo < 0 || lo >= nact || prefix[lo] > t) {
+        lo = 0;
+        int hi = nact;   // binary search: prefix[lo] <= t < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= t) lo = mid; else hi = mid;
+        }
+        return lo;
+    }
+    while (lo + 1 < nact && prefix[lo + 1] <= t) ++lo;
+    return lo;
+}
 
 cudaError_t launch_batch_cheb(const BatchDev& B, const double* p, const double* q, double* out, bool first,
                               cudaStream_t st);
-cudaError_t launch_batch_gram(const BatchDev& B, int s, int nu, int solver, const double* P, cudaStream_t st);
+cudaError_t launch_batch_gram(const BatchDev& B, int s, int nu, int solver, bool moments, const double* P,
+                              cudaStream_t st);
 cudaError_t launch_batch_update(const BatchDev& B, int s, const double* P, double* x, cudaStream_t st);
 cudaError_t launch_batch_residual(const BatchDev& B, const double* b, const double* x, double* r, int mode,
                                   cudaStream_t st);
 cudaError_t launch_batch_init(const BatchDev& B, double tol_sq, int max_outer, cudaStream_t st);
 cudaError_t launch_batch_cond(cudaGraphConditionalHandle h, const int* running, cudaStream_t st);
+cudaError_t launch_batch_compact(const BatchDev& B, cudaStream_t st);
 int batch_gram_m(int s);
 
 }  // namespace sstep

@@ -433,6 +433,24 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram(const T* __restrict__ 
     if (warp == 0) gram_finish<S, DV, MOM>(tot, gp, ctl, smem);
 }
 
+// Resident blocks per SM of the kernel variant g selects (for sizing the grid).
+template <int S>
+int gram_occupancy_s(const GramArgs& g) {
+    int occ = 1;
+    const bool mom = g.form == SSTEP_GRAM_FORM_MOMENTS;
+    cudaError_t e;
+#define SSTEP_OCC(DV, T, MOM) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram<S, DV, T, MOM>, GRAM_THREADS, 0)
+    if (g.fp32) {
+        if (g.dvec) { if (mom) SSTEP_OCC(true, float, true); else SSTEP_OCC(true, float, false); }
+        else { if (mom) SSTEP_OCC(false, float, true); else SSTEP_OCC(false, float, false); }
+    } else {
+        if (g.dvec) { if (mom) SSTEP_OCC(true, double, true); else SSTEP_OCC(true, double, false); }
+        else { if (mom) SSTEP_OCC(false, double, true); else SSTEP_OCC(false, double, false); }
+    }
+#undef SSTEP_OCC
+    return (e == cudaSuccess && occ > 0) ? occ : 1;
+}
+
 template <int S>
 cudaError_t launch_gram_s(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st) {
     GramParams gp;

@@ -13,16 +13,40 @@ SSTEP_EXTERN_GRAM(21) SSTEP_EXTERN_GRAM(22) SSTEP_EXTERN_GRAM(23) SSTEP_EXTERN_G
 SSTEP_EXTERN_GRAM(26) SSTEP_EXTERN_GRAM(27) SSTEP_EXTERN_GRAM(28) SSTEP_EXTERN_GRAM(29) SSTEP_EXTERN_GRAM(30)
 SSTEP_EXTERN_GRAM(31) SSTEP_EXTERN_GRAM(32)
 #undef SSTEP_EXTERN_GRAM
+#define SSTEP_EXTERN_OCC(S) extern template int gram_occupancy_s<S>(const GramArgs&);
+SSTEP_EXTERN_OCC(1) SSTEP_EXTERN_OCC(2) SSTEP_EXTERN_OCC(3) SSTEP_EXTERN_OCC(4) SSTEP_EXTERN_OCC(5)
+SSTEP_EXTERN_OCC(6) SSTEP_EXTERN_OCC(7) SSTEP_EXTERN_OCC(8) SSTEP_EXTERN_OCC(9) SSTEP_EXTERN_OCC(10)
+SSTEP_EXTERN_OCC(11) SSTEP_EXTERN_OCC(12) SSTEP_EXTERN_OCC(13) SSTEP_EXTERN_OCC(14) SSTEP_EXTERN_OCC(15)
+SSTEP_EXTERN_OCC(16) SSTEP_EXTERN_OCC(17) SSTEP_EXTERN_OCC(18) SSTEP_EXTERN_OCC(19) SSTEP_EXTERN_OCC(20)
+SSTEP_EXTERN_OCC(21) SSTEP_EXTERN_OCC(22) SSTEP_EXTERN_OCC(23) SSTEP_EXTERN_OCC(24) SSTEP_EXTERN_OCC(25)
+SSTEP_EXTERN_OCC(26) SSTEP_EXTERN_OCC(27) SSTEP_EXTERN_OCC(28) SSTEP_EXTERN_OCC(29) SSTEP_EXTERN_OCC(30)
+SSTEP_EXTERN_OCC(31) SSTEP_EXTERN_OCC(32)
+#undef SSTEP_EXTERN_OCC
 
 static int gram_m(int s, bool dvec) { return s * (s + 1) / 2 + s + (dvec ? s : 0); }   // >= the moments form's 2s (+ s)
 
+static int gram_occupancy(const GramArgs& g) {
+    switch (g.s) {
+#define SSTEP_CASE(S) case S: return gram_occupancy_s<S>(g);
+        SSTEP_CASE(1) SSTEP_CASE(2) SSTEP_CASE(3) SSTEP_CASE(4) SSTEP_CASE(5) SSTEP_CASE(6) SSTEP_CASE(7)
+        SSTEP_CASE(8) SSTEP_CASE(9) SSTEP_CASE(10) SSTEP_CASE(11) SSTEP_CASE(12) SSTEP_CASE(13) SSTEP_CASE(14)
+        SSTEP_CASE(15) SSTEP_CASE(16) SSTEP_CASE(17) SSTEP_CASE(18) SSTEP_CASE(19) SSTEP_CASE(20) SSTEP_CASE(21)
+        SSTEP_CASE(22) SSTEP_CASE(23) SSTEP_CASE(24) SSTEP_CASE(25) SSTEP_CASE(26) SSTEP_CASE(27) SSTEP_CASE(28)
+        SSTEP_CASE(29) SSTEP_CASE(30) SSTEP_CASE(31) SSTEP_CASE(32)
+#undef SSTEP_CASE
+        default: return 1;
+    }
+}
+
 int gram_blocks(const GramArgs& g, int sm_count) {
-    // one 512-thread block per SM (the kernel asks for <= 128 registers per thread),
-    // fewer when the vector is short (one element per thread of the block at most)
+    // as many 512-thread blocks as fit on the SMs at once (the variant's register use decides:
+    // the FP64 forms are FP64-pipe bound with one, the lighter variants need more memory
+    // parallelism), fewer when the vector is short (one element per thread at most)
     const int64_t per_block = (int64_t)GRAM_WARPS * 32;
     int64_t want = (g.n + per_block - 1) / per_block;
     if (want < 1) want = 1;
-    return (int)(want < sm_count ? want : sm_count);
+    const int64_t cap = (int64_t)sm_count * gram_occupancy(g);
+    return (int)(want < cap ? want : cap);
 }
 
 size_t gram_partials_needed(const GramArgs& g, int nblocks) { return (size_t)nblocks * gram_m(g.s, g.dvec); }

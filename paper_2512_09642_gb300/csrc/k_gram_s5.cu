@@ -6,4 +6,8 @@ template cudaError_t launch_gram_s<17>(const GramArgs&, double*, Ctl*, int, cuda
 template cudaError_t launch_gram_s<18>(const GramArgs&, double*, Ctl*, int, cudaStream_t);
 template cudaError_t launch_gram_s<19>(const GramArgs&, double*, Ctl*, int, cudaStream_t);
 template cudaError_t launch_gram_s<20>(const GramArgs&, double*, Ctl*, int, cudaStream_t);
+template int gram_occupancy_s<17>(const GramArgs&);
+template int gram_occupancy_s<18>(const GramArgs&);
+template int gram_occupancy_s<19>(const GramArgs&);
+template int gram_occupancy_s<20>(const GramArgs&);
 }  // namespace sstep

@@ -1,11 +1,16 @@
 // Operator kernels: the Chebyshev matrix-powers step (Section 2, Definition "Chebyshev
 // Polynomial Basis"), r = b - A x with its norm, and y = A x, for CSR matrices and for the
-// matrix-free 5-/7-point Poisson and cell-centred diffusion stencils.
+// matrix-free 5-/7-point Poisson, 9-/27-point box Poisson (Section 8's operator) and
+// cell-centred diffusion stencils.
 //
 // GB300 notes: FP64 issues at ~1/74 of the FP32 rate on this part, so the FP64 forms are
-// written to minimise FP64 instructions per unknown (Poisson step: 5 adds + 2 FMAs), and
-// every index is computed from the launch grid, never by 64-bit division. Stencil kernels
-// march along z with the z-neighbours held in registers; x/y neighbours come through L1.
+// written to minimise FP64 instructions per unknown (7-point step: 5 adds + 2 FMAs; 27-point
+// step: about 9 operations through separable box sums), and every index is computed from
+// the launch grid, never by 64-bit division. Stencil kernels march along z with the
+// z-neighbours (or z-plane sums) held in registers. The 5-/7-point and diffusion kernels read
+// their x/y neighbours through L1 (staging planes in shared memory made them slower: the
+// barriers expose each plane's load latency); the box kernels stage each plane with its
+// halo in shared memory, where it serves 9 products per point.
 #include <type_traits>
 
 #include "kernels.h"
@@ -297,6 +302,166 @@ __global__ void __launch_bounds__(BX* BY) k_apply_stencil(const double* __restri
     }
 }
 
+// --- box stencil --------------------------------------------------------------------
+// Every one of the 3^d - 1 grid points of the unit box around a point is a neighbour with
+// weight -1 and the diagonal is 3^d - 1, so A p = 3^d p - B with B the sum of p over the whole
+// box (0 outside the grid). B is formed separably: row sums R over x of each plane staged in
+// shared memory, plane sums S over y of R (the 3 x 3 in-plane box), B = S(k-1) + S(k) + S(k+1)
+// over z. A block computes S once per plane it touches (KB + 2 planes for KB outputs), about 9
+// FP64 additions and FMAs per unknown instead of 26 neighbour additions. The values of the
+// next plane (and the vector read with each output) are loaded into registers one plane
+// ahead, so the two barriers per plane do not wait on memory.
+constexpr int KB = 16;   // z planes per block of the box kernels
+
+// One thread's share of a staged plane: its point, and the halo point it stages when it sits
+// on the tile's x edge (hx), y edge (hy) or is one of the four corner loaders (hc).
+template <typename T> struct BoxRegs { T c, hx, hy, hc; };
+
+template <typename T>
+__device__ __forceinline__ BoxRegs<T> box_load(const T* __restrict__ p, int64_t sxy, int k, bool valid, int i0, int j0,
+                                               int nx, int ny) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = i0 + tx, j = j0 + ty;
+    BoxRegs<T> v{T(0), T(0), T(0), T(0)};
+    if (!valid) return v;
+    const T* pk = p + sxy * k;
+    if (i < nx && j < ny) v.c = ldg(pk + i + (int64_t)nx * j);
+    if (tx == 0 && i0 > 0 && j < ny) v.hx = ldg(pk + (i0 - 1) + (int64_t)nx * j);
+    if (tx == BX - 1 && i0 + BX < nx && j < ny) v.hx = ldg(pk + (i0 + BX) + (int64_t)nx * j);
+    if (ty == 0 && j0 > 0 && i < nx) v.hy = ldg(pk + i + (int64_t)nx * (j0 - 1));
+    if (ty == BY - 1 && j0 + BY < ny && i < nx) v.hy = ldg(pk + i + (int64_t)nx * (j0 + BY));
+    if (ty == 1 && tx < 4) {   // the four halo corners
+        const int ci = (tx & 1) ? i0 + BX : i0 - 1;
+        const int cj = (tx >> 1) ? j0 + BY : j0 - 1;
+        if (ci >= 0 && ci < nx && cj >= 0 && cj < ny) v.hc = ldg(pk + ci + (int64_t)nx * cj);
+    }
+    return v;
+}
+
+// S (the in-plane 3 x 3 box sum) at this thread's point from the plane held in v. Two block
+// barriers; sp / sr may be reused after it returns.
+template <typename T>
+__device__ __forceinline__ T box_plane_sum(T (*sp)[BX + 2], T (*sr)[BX], const BoxRegs<T>& v) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    sp[ty + 1][tx + 1] = v.c;
+    if (tx == 0) sp[ty + 1][0] = v.hx;
+    if (tx == BX - 1) sp[ty + 1][BX + 1] = v.hx;
+    if (ty == 0) sp[0][tx + 1] = v.hy;
+    if (ty == BY - 1) sp[BY + 1][tx + 1] = v.hy;
+    if (ty == 1 && tx < 4) sp[(tx >> 1) ? BY + 1 : 0][(tx & 1) ? BX + 1 : 0] = v.hc;
+    __syncthreads();
+    sr[ty + 1][tx] = (sp[ty + 1][tx] + sp[ty + 1][tx + 1]) + sp[ty + 1][tx + 2];
+    if (ty == 0) sr[0][tx] = (sp[0][tx] + sp[0][tx + 1]) + sp[0][tx + 2];
+    if (ty == BY - 1) sr[BY + 1][tx] = (sp[BY + 1][tx] + sp[BY + 1][tx + 1]) + sp[BY + 1][tx + 2];
+    __syncthreads();
+    return (sr[ty][tx] + sr[ty + 1][tx]) + sr[ty + 2][tx];
+}
+
+// Marches the block's tile over its z slab (3D: planes k0 .. k1 - 1; 2D: the one plane) and
+// calls emit(k, p_k, B_k, extra_k) for each, where extra_k = pre(k) was read one plane ahead.
+template <typename T, int DIM, typename Pre, typename Emit>
+__device__ __forceinline__ void box_march(const T* __restrict__ p, int nx, int ny, int nz, Pre pre, Emit emit) {
+    __shared__ T sp[BY + 2][BX + 2];
+    __shared__ T sr[BY + 2][BX];
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int64_t sxy = (int64_t)nx * ny;
+    if (DIM == 2) {
+        const T ex = pre(0);
+        const BoxRegs<T> v = box_load<T>(p, sxy, 0, true, i0, j0, nx, ny);
+        emit(0, v.c, box_plane_sum<T>(sp, sr, v), ex);
+        return;
+    }
+    const int k0 = blockIdx.z * KB, k1 = min(nz, k0 + KB);
+    // window over planes kk = k0 - 1 .. k1: S(kk - 2) = sa, S(kk - 1) = sb, p(kk - 1) = pb
+    T sa = T(0), sb = T(0), pb = T(0), eb = T(0);
+    BoxRegs<T> cur = box_load<T>(p, sxy, k0 - 1, k0 > 0, i0, j0, nx, ny);
+    for (int kk = k0 - 1; kk <= k1; ++kk) {
+        const bool nvalid = kk + 1 <= k1 && kk + 1 < nz;
+        const BoxRegs<T> nxt = box_load<T>(p, sxy, kk + 1, nvalid, i0, j0, nx, ny);
+        const T ecur = (kk >= k0 && kk < k1) ? pre(kk) : T(0);
+        const bool here = kk >= 0 && kk < nz;   // uniform over the block
+        const T sc = here ? box_plane_sum<T>(sp, sr, cur) : T(0);
+        if (kk - 1 >= k0) emit(kk - 1, pb, (sa + sb) + sc, eb);
+        sa = sb;
+        sb = sc;
+        pb = cur.c;
+        eb = ecur;
+        cur = nxt;
+    }
+}
+
+// Chebyshev step: out = ca p + cb B - q (q absent in the first step).
+template <typename T, int DIM, bool FIRST>
+__global__ void __launch_bounds__(BX* BY) k_cheb_box(const T* __restrict__ p, const T* __restrict__ q,
+                                                     T* __restrict__ out, int nx, int ny, int nz, T ca, T cb,
+                                                     const Ctl* __restrict__ ctl) {
+    if (ctl->done) return;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const bool in = i < nx && j < ny;
+    const int64_t ij = i + (int64_t)nx * j, sxy = (int64_t)nx * ny;
+    box_march<T, DIM>(
+        p, nx, ny, nz, [&](int k) { return (FIRST || !in) ? T(0) : ldg(q + ij + sxy * k); },
+        [&](int k, T pc, T B, T qv) {
+            if (in) out[ij + sxy * k] = FIRST ? fma(cb, B, ca * pc) : fma(cb, B, fma(ca, pc, -qv));
+        });
+}
+
+// r = b - A x = b - (3^d x - B) with ||r||^2 (residual modes as k_residual_stencil).
+template <int DIM>
+__global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restrict__ b, const double* __restrict__ x,
+                                                         double* __restrict__ r, float* __restrict__ r32, int nx,
+                                                         int ny, int nz, double* partials, Ctl* ctl, int mode) {
+    if (mode == 2 && ctl->done) return;
+    int kscale = 0;   // scale_next = 2^kscale
+    if (mode == 2) {
+        frexp(ctl->scale_next, &kscale);
+        kscale -= 1;
+    }
+    const double dfull = DIM == 3 ? 27.0 : 9.0;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const bool in = i < nx && j < ny;
+    const int64_t ij = i + (int64_t)nx * j, sxy = (int64_t)nx * ny;
+    double ss = 0.0;
+    box_march<double, DIM>(
+        x, nx, ny, nz, [&](int k) { return in ? ldg(b + ij + sxy * k) : 0.0; },
+        [&](int k, double pc, double B, double bv) {
+            if (!in) return;
+            const int64_t e = ij + sxy * k;
+            const double rv = bv - fma(dfull, pc, -B);
+            if (r) r[e] = rv;
+            if (r32) r32[e] = d2f_scaled(rv, kscale);
+            ss = fma(rv, rv, ss);
+        });
+    __shared__ double sh[BX * BY / 32];
+    double v = warp_sum(ss);
+    const int t = threadIdx.x + BX * threadIdx.y;
+    if ((t & 31) == 0) sh[t >> 5] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (t == 0)
+        for (int k = 0; k < BX * BY / 32; ++k) tot += sh[k];
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, nblk);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(BX* BY) k_apply_box(const double* __restrict__ x, double* __restrict__ y, int nx,
+                                                      int ny, int nz) {
+    const double dfull = DIM == 3 ? 27.0 : 9.0;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const bool in = i < nx && j < ny;
+    const int64_t ij = i + (int64_t)nx * j, sxy = (int64_t)nx * ny;
+    box_march<double, DIM>(
+        x, nx, ny, nz, [&](int) { return 0.0; },
+        [&](int k, double pc, double B, double) {
+            if (in) y[ij + sxy * k] = fma(dfull, pc, -B);
+        });
+}
+
+dim3 box_grid(const OpDesc& op) {
+    return dim3((op.nx + BX - 1) / BX, (op.ny + BY - 1) / BY, op.dim == 3 ? (op.nz + KB - 1) / KB : 1);
+}
+
 __global__ void __launch_bounds__(RB) k_apply_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                                                   const double* __restrict__ vals, const double* __restrict__ x,
                                                   double* __restrict__ y, int64_t n) {
@@ -369,6 +534,23 @@ void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, dou
 template <typename T>
 cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, double theta, double sigma, bool first,
                              bool jacobi, const Ctl* ctl, cudaStream_t st) {
+    if (op.kind == OP_STENCIL && op.box) {
+        // c (M^-1 A p - sigma p) = c (D + 1 - sigma) p - c B without a preconditioner and
+        // c (1 - sigma + 1 / D) p - (c / D) B with Jacobi (D = 3^dim - 1)
+        const double c = first ? theta : 2.0 * theta;
+        const double D = op.dim == 3 ? 26.0 : 8.0;
+        const T ca = (T)(jacobi ? c * (1.0 - sigma) + c / D : c * (D + 1.0 - sigma));
+        const T cb = (T)(jacobi ? -c / D : -c);
+        const dim3 grid = box_grid(op), block(BX, BY);
+        if (op.dim == 3) {
+            if (first) k_cheb_box<T, 3, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
+            else k_cheb_box<T, 3, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
+        } else {
+            if (first) k_cheb_box<T, 2, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
+            else k_cheb_box<T, 2, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
+        }
+        return cudaGetLastError();
+    }
     if (op.kind == OP_STENCIL) {
         const bool poisson = op.wx == nullptr;
         if (op.dim == 3) {
@@ -400,6 +582,10 @@ template cudaError_t launch_cheb_step<float>(const OpDesc&, const float*, const 
                                              bool, const Ctl*, cudaStream_t);
 
 size_t residual_partials_needed(const OpDesc& op) {
+    if (op.kind == OP_STENCIL && op.box) {
+        const dim3 g = box_grid(op);
+        return (size_t)g.x * g.y * g.z;
+    }
     if (op.kind == OP_STENCIL) {
         const dim3 g = stencil_grid(op);
         return (size_t)g.x * g.y * g.z;
@@ -409,6 +595,12 @@ size_t residual_partials_needed(const OpDesc& op) {
 
 cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, double* r, float* r32,
                             double* partials, Ctl* ctl, int mode, cudaStream_t st) {
+    if (op.kind == OP_STENCIL && op.box) {
+        const dim3 grid = box_grid(op), block(BX, BY);
+        if (op.dim == 3) k_residual_box<3><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode);
+        else k_residual_box<2><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode);
+        return cudaGetLastError();
+    }
     if (op.kind == OP_STENCIL) {
         const dim3 grid = stencil_grid(op), block(BX, BY);
         const Faces<double> f = faces_of<double>(op);
@@ -444,6 +636,12 @@ cudaError_t launch_convert_check(const double* in, int k, float* out, double* ba
 }
 
 cudaError_t launch_apply(const OpDesc& op, const double* x, double* y, cudaStream_t st) {
+    if (op.kind == OP_STENCIL && op.box) {
+        const dim3 grid = box_grid(op), block(BX, BY);
+        if (op.dim == 3) k_apply_box<3><<<grid, block, 0, st>>>(x, y, op.nx, op.ny, op.nz);
+        else k_apply_box<2><<<grid, block, 0, st>>>(x, y, op.nx, op.ny, op.nz);
+        return cudaGetLastError();
+    }
     if (op.kind == OP_STENCIL) {
         const dim3 grid = stencil_grid(op), block(BX, BY);
         const Faces<double> f = faces_of<double>(op);

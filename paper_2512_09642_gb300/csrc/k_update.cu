@@ -73,9 +73,12 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle handle, const Ctl* __rest
     cudaGraphSetConditional(handle, ctl->done == RUNNING ? 1u : 0u);
 }
 
-int blocks_for(int64_t n) {
+// Grid: per_sm blocks per SM at most (the FP64 update is FP64-pipe bound and runs best with
+// 4, the HBM-bound mixed update with 8 in flight), fewer for short vectors.
+int blocks_for(int64_t n, int per_sm) {
     const int64_t b = (n + UB - 1) / UB;
-    return (int)(b < 152 * 4 ? (b < 1 ? 1 : b) : 152 * 4);
+    const int64_t cap = 152 * (int64_t)per_sm;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 }  // namespace
@@ -87,7 +90,7 @@ cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, 
 
 cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
                                 cudaStream_t st) {
-    const int nb = blocks_for(n);
+    const int nb = blocks_for(n, 8);
     switch (s) {
 #define SSTEP_CASE(S) case S: k_update_mixed<S><<<nb, UB, 0, st>>>(P, ld, n, x, ctl); break;
         SSTEP_CASE(1) SSTEP_CASE(2) SSTEP_CASE(3) SSTEP_CASE(4) SSTEP_CASE(5) SSTEP_CASE(6) SSTEP_CASE(7)
@@ -106,9 +109,9 @@ cudaError_t launch_update(const UpdateArgs& u, const Ctl* ctl, cudaStream_t st) 
     const double* P = (const double*)u.P;
     double* r = (double*)u.P;   // column 0
     if (u.dvec)
-        k_update_f64<true><<<blocks_for(u.n), UB, 0, st>>>(P, u.ld, u.s, u.diag, u.n, u.x, r, u.skip_r, ctl);
+        k_update_f64<true><<<blocks_for(u.n, 4), UB, 0, st>>>(P, u.ld, u.s, u.diag, u.n, u.x, r, u.skip_r, ctl);
     else
-        k_update_f64<false><<<blocks_for(u.n), UB, 0, st>>>(P, u.ld, u.s, nullptr, u.n, u.x, r, u.skip_r, ctl);
+        k_update_f64<false><<<blocks_for(u.n, 4), UB, 0, st>>>(P, u.ld, u.s, nullptr, u.n, u.x, r, u.skip_r, ctl);
     return cudaGetLastError();
 }
 

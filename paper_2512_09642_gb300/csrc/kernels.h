@@ -16,6 +16,7 @@ struct OpDesc {
     const float* vals32;   // FP32 copy (mixed precision), may be null
     // stencil
     int dim, nx, ny, nz;
+    int box;               // 1: box stencil (all 3^dim - 1 neighbours, Poisson weights)
     const double* wx;      // face weights, null for the Poisson stencil
     const double* wy;
     const double* wz;

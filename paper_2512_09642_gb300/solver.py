@@ -16,15 +16,18 @@ class SStepCG:
     """Chebyshev-basis s-step CG (arXiv 2512.09642, Section 2) on one CUDA device.
 
     Exactly one of `csr=(rowptr, colind, vals)` (int32, int32, float64 CUDA tensors) or
-    `grid=(nx, ny[, nz])` (matrix-free Poisson, or diffusion with `kappa`) is given.
+    `grid=(nx, ny[, nz])` (matrix-free Poisson, or diffusion with `kappa`; stencil="box" gives
+    the 9-/27-point box Poisson operator of Section 8) is given.
     Options are the fields of sstep_cg_opts (s, nu, tol, bounds_mode, lambda_min, ...);
     `bounds=(lmin, lmax)` is shorthand for bounds_mode="given".
     """
 
     def __init__(self, *, csr=None, grid=None, kappa: Optional[torch.Tensor] = None, bounds=None, stream=None,
-                 **opts):
+                 stencil: str = "star", **opts):
         if (csr is None) == (grid is None):
             raise ValueError("give exactly one of csr= or grid=")
+        if stencil not in ("star", "box") or (stencil == "box" and kappa is not None):
+            raise ValueError("stencil is 'star' (5/7-point or diffusion) or 'box' (9/27-point Poisson)")
         if bounds is not None:
             opts.update(bounds_mode="given", lambda_min=float(bounds[0]), lambda_max=float(bounds[1]))
         self.opts = abi.sstep_cg_default_opts(**opts)
@@ -42,7 +45,10 @@ class SStepCG:
             if kappa is not None:
                 self._keep.append(kappa)
             self.n = nx * ny * nz
-            self.h = abi.sstep_cg_create_stencil(dim, nx, ny, nz, kappa, self.opts, stream)
+            if stencil == "box":
+                self.h = abi.sstep_cg_create_box_stencil(dim, nx, ny, nz, self.opts, stream)
+            else:
+                self.h = abi.sstep_cg_create_stencil(dim, nx, ny, nz, kappa, self.opts, stream)
         self.device = torch.device("cuda", torch.cuda.current_device())
 
     @property

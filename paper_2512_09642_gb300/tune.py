@@ -1,19 +1,20 @@
-"""Autotuner for the batched form: picks s, nu and the launch shapes (unknowns per Gram/update
-work item, resident blocks per SM of the stencil kernels) for a given batch.
+"""Autotuner for the batched form: picks s, nu, the Gram form and the launch shapes (unknowns
+per Gram/update work item, resident blocks per SM of the stencil kernels) for a given batch.
 
-For each candidate it runs two short probes on a subsample of the batch (the largest systems,
-which set the batch's time, plus a spread of smaller ones): K1 and K2 > K1 outer iterations
-with tolerance 0, through the library's batched solve. From them it takes
-  * the device time per unknown and outer iteration, c = (t(K2) - t(K1)) / (sum_i n_i (K2 - K1)),
-  * each system's contraction per outer iteration, rho_i = (r_i(K2) / r_i(K1))^(1 / (K2 - K1)),
-    measured after the first K1 outer iterations, where the smooth error modes dominate,
-and predicts the time to tol as c * sum_i n_i N_i with N_i = K1 + log(tol / r_i(K1)) / log(rho_i)
-(converged systems leave the batch, so each costs only its own outer iterations). The
-candidate with the smallest prediction wins. All solves run in libsstep_cg.so.
+For each candidate it solves a subsample of the batch to the tolerance with the library's
+batched solve (the largest systems, which set the batch's critical path, plus a spread of
+smaller ones). From that run it takes
+  * each sampled system's outer-iteration count N_i, fitted as N = a n^b over system size n
+    (outer counts of these solves grow as a power of the grid size), and
+  * the device time per unknown and outer iteration, c = t / sum_i n_i N_i,
+and predicts the batch's time as c * sum_j n_j N(n_j) (a converged system leaves the batch,
+so each costs only its own outer iterations). The candidate with the smallest prediction
+wins. Short probes of a few outer iterations are not used: the contraction of the early
+outer iterations is much faster than the asymptotic one and mispredicts the count by
+orders of magnitude. All solves run in libsstep_cg.so.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 from typing import List, Optional, Sequence
 
@@ -23,10 +24,9 @@ import torch
 from . import abi
 
 DEFAULT_CANDIDATES = [
-    {"s": s, "nu": nu, "batch_chunk": chunk, "batch_ctas_per_sm": ctas}
-    for (s, nu) in ((4, 20), (8, 20), (8, 30), (12, 30), (16, 30))
-    for chunk in (8192, 32768)
-    for ctas in (4, 6)
+    {"s": s, "nu": nu, "gram_form": form, "batch_chunk": 8192, "batch_ctas_per_sm": 6}
+    for (s, nu) in ((6, 20), (8, 20), (8, 30), (10, 25), (12, 30))
+    for form in ("direct", "moments")
 ]
 
 
@@ -38,20 +38,20 @@ class TuneResult:
     sample: List[int] = field(default_factory=list)
 
 
-def pick_sample(sizes: Sequence[int], k: int = 16) -> List[int]:
+def pick_sample(sizes: Sequence[int], k: int = 12) -> List[int]:
     """The k//2 largest systems and k - k//2 others spread evenly over the remaining sizes."""
     order = list(np.argsort(-np.asarray(sizes), kind="stable"))
-    big = order[: k // 2]
+    chosen = order[: k // 2]
     rest = order[k // 2:]
-    m = k - len(big)
+    m = k - len(chosen)
     if m > 0 and rest:
         idx = np.linspace(0, len(rest) - 1, num=min(m, len(rest))).round().astype(int)
-        big += [rest[i] for i in idx]
-    return sorted(set(int(i) for i in big))
+        chosen += [rest[i] for i in idx]
+    return sorted(set(int(i) for i in chosen))
 
 
-def _probe(grids, kappas, bs, cand: dict, outers: int, stream=None):
-    opts = abi.sstep_cg_default_opts(tol=1e-30, max_outer=outers, use_graph=1, **cand)
+def _solve_sample(grids, kappas, bs, cand: dict, tol: float, max_outer: int, stream=None):
+    opts = abi.sstep_cg_default_opts(tol=tol, max_outer=max_outer, use_graph=1, **cand)
     h = abi.sstep_cg_batch_create(grids, kappas, opts, stream)
     try:
         offs, total, _ = abi.sstep_cg_batch_layout(h, len(grids))
@@ -59,41 +59,34 @@ def _probe(grids, kappas, bs, cand: dict, outers: int, stream=None):
         for bi, o in zip(bs, offs):
             b[o:o + bi.numel()] = bi
         x = torch.zeros_like(b)
-        abi.sstep_cg_batch_solve(h, b, x, len(grids))          # warm (graph capture, lazy loading)
-        x.zero_()
         infos, summary = abi.sstep_cg_batch_solve(h, b, x, len(grids))
     finally:
         abi.sstep_cg_batch_destroy(h)
-    return summary["ms"], [i["rel_res_true"] for i in infos]
+    return summary["ms"], [i["outer_iters"] for i in infos], [i["status"] for i in infos]
 
 
-def tune(grids, kappas, bs, tol: float = 1e-8, candidates: Optional[list] = None, sample: int = 16,
-         k1: int = 20, k2: int = 60, stream=None) -> TuneResult:
+def tune(grids, kappas, bs, tol: float = 1e-8, candidates: Optional[list] = None, sample: int = 12,
+         max_outer: int = 40000, stream=None) -> TuneResult:
     """grids: list of (nx, ny[, nz]); kappas: CUDA tensors or None; bs: CUDA right-hand sides."""
     candidates = candidates or DEFAULT_CANDIDATES
-    sizes = [int(np.prod(g)) for g in grids]
-    idx = pick_sample(sizes, sample)
+    sizes = np.array([int(np.prod(g)) for g in grids], dtype=np.float64)
+    idx = pick_sample(list(sizes), sample)
     sg = [grids[i] for i in idx]
     sk = [kappas[i] for i in idx]
     sb = [bs[i] for i in idx]
-    # the sample stands for the whole batch: scale by unknowns
-    scale = sum(sizes) / sum(sizes[i] for i in idx)
+    n_s = sizes[idx]
     table = []
     for cand in candidates:
-        t1, r1 = _probe(sg, sk, sb, cand, k1, stream)
-        t2, r2 = _probe(sg, sk, sb, cand, k2, stream)
-        n_s = [sizes[i] for i in idx]
-        c = max(t2 - t1, 1e-6) / (sum(n_s) * (k2 - k1))          # ms per unknown-outer
-        work = 0.0
-        for n, a, b in zip(n_s, r1, r2):
-            if b <= tol or a <= 0.0:
-                N = k2
-            else:
-                rho = (b / a) ** (1.0 / (k2 - k1)) if b < a else 1.0 - 1e-9
-                N = k1 + math.log(tol / a) / math.log(rho) if rho < 1.0 else 1e9
-            work += n * N
-        pred_ms = c * work * scale
-        table.append(dict(cand, ms_per_unknown_outer=c, predicted_s=pred_ms / 1e3))
+        ms, outers, status = _solve_sample(sg, sk, sb, cand, tol, max_outer, stream)
+        N = np.maximum(np.asarray(outers, dtype=np.float64), 1.0)
+        ok = all(st == "SSTEP_OK" for st in status)
+        # N = a n^b by least squares in log-log
+        b_, a_ = np.polyfit(np.log(n_s), np.log(N), 1) if len(set(n_s)) > 1 else (0.0, np.log(N.mean()))
+        N_all = np.exp(a_) * sizes ** b_
+        c = ms / float(np.sum(n_s * N))                      # ms per unknown-outer on the sample
+        pred = c * float(np.sum(sizes * N_all)) / 1e3
+        table.append(dict(cand, sample_ms=ms, fit_exponent=float(b_), predicted_s=pred if ok else float("inf"),
+                          sample_max_outer=int(N.max())))
     best = min(table, key=lambda r: r["predicted_s"])
-    params = {k: best[k] for k in ("s", "nu", "batch_chunk", "batch_ctas_per_sm")}
+    params = {k: best[k] for k in ("s", "nu", "gram_form", "batch_chunk", "batch_ctas_per_sm")}
     return TuneResult(best=params, predicted_s=best["predicted_s"], table=table, sample=idx)

@@ -1,9 +1,12 @@
-"""Writes tests/golden/oracle_outer_counts.txt: outer-iteration counts, final relative
+"""Writes tests/golden/oracle_outer_counts.txt (7-point Poisson, bounds gersh_lanczos10) and,
+with `box` as first argument, tests/golden/oracle_outer_counts_box.txt (27-point Poisson,
+the Lanczos-10 bounds with 10% margins of Section 8): outer-iteration counts, final relative
 residuals and per-outer CPU time of the oracle on the benchmark workloads, run to
-convergence (tol 1e-8). Calls only oracle/ and workloads/. Slow: the 256^3 case takes
-hours on one CPU core, which is why its result is stored.
+convergence (tol 1e-8). Calls only oracle/ and workloads/. Slow: the 256^3 and 230^3 cases
+take hours on one CPU core, which is why their results are stored.
 
     python tests/golden/make_oracle_outer_counts.py [sides...]
+    python tests/golden/make_oracle_outer_counts.py box [sides...]
 """
 import os
 import sys
@@ -15,12 +18,14 @@ import oracle as O  # noqa: E402
 from oracle import spectral as OS  # noqa: E402
 from workloads import problems as W  # noqa: E402
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_outer_counts.txt")
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "oracle_outer_counts.txt")
+OUT_BOX = os.path.join(HERE, "oracle_outer_counts_box.txt")
 
 
-def run(name, p, s, nu):
+def run(name, p, s, nu, bounds="gersh_lanczos10"):
     op = O.Operator(*p.csr())
-    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+    lam = OS.bounds(op, bounds, W.lanczos_start(p.n))
     t0 = time.time()
     res = O.solve(op, p.b, s=s, nu=nu, lam_min=lam[0], lam_max=lam[1], tol=1e-8)
     dt = time.time() - t0
@@ -31,7 +36,18 @@ def run(name, p, s, nu):
     return line
 
 
-if __name__ == "__main__":
+def main_box(sides):
+    lines = ["# oracle (FP64, 1 thread) to ||r||/||r0|| < 1e-8; 27-point Poisson, Jacobi, bounds lanczos10 "
+             "(seed 5000)", "# written by tests/golden/make_oracle_outer_counts.py box"]
+    for side in sides:
+        lines.append(run(f"poisson27_{side}", W.poisson27(side), 8, 25, bounds="lanczos10"))
+        with open(OUT_BOX, "w") as f:
+            f.write("\n".join(lines) + "\n")
+
+
+if __name__ == "__main__" and sys.argv[1:2] == ["box"]:
+    main_box([int(v) for v in sys.argv[2:]] or [64, 128, 230])
+elif __name__ == "__main__":
     sides = [int(v) for v in sys.argv[1:]] or [64, 128, 256]
     lines = ["# oracle (FP64, 1 thread) to ||r||/||r0|| < 1e-8; Jacobi, bounds gersh_lanczos10 (seed 5000)",
              "# written by tests/golden/make_oracle_outer_counts.py"]

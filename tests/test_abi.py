@@ -89,6 +89,15 @@ def test_invalid_grid_rejected_on_host(abi, grid):
     with pytest.raises(abi.SStepError) as ei:
         abi.sstep_cg_create_stencil(*grid, None, abi.sstep_cg_default_opts(), stream=0)
     assert ei.value.status == 1
+    with pytest.raises(abi.SStepError) as ei:
+        abi.sstep_cg_create_box_stencil(*grid, abi.sstep_cg_default_opts(), stream=0)
+    assert ei.value.status == 1
+
+
+def test_box_stencil_invalid_options_rejected_on_host(abi):
+    with pytest.raises(abi.SStepError) as ei:
+        abi.sstep_cg_create_box_stencil(3, 8, 8, 8, abi.sstep_cg_default_opts(s=0), stream=0)
+    assert ei.value.status == 1
 
 
 def test_invalid_csr_rejected_on_host(abi):

@@ -51,11 +51,12 @@ def test_batch_bounds_match_single_system_estimates():
     abi.sstep_cg_batch_destroy(h)
 
 
+@pytest.mark.parametrize("gram_form", ["direct", "moments"])
 @pytest.mark.parametrize("s,nu", [(4, 20), (8, 20)])
-def test_batch_first_iterates_match_oracle_per_system(s, nu):
+def test_batch_first_iterates_match_oracle_per_system(s, nu, gram_form):
     from paper_2512_09642_gb300 import abi
     probs = _batch_problems()
-    h, kap, offs, total, lam, b = _make_batch(probs, s=s, nu=nu, tol=1e-30, max_outer=3)
+    h, kap, offs, total, lam, b = _make_batch(probs, s=s, nu=nu, tol=1e-30, max_outer=3, gram_form=gram_form)
     x = torch.zeros(total, dtype=torch.float64, device="cuda")
     infos, summary = abi.sstep_cg_batch_solve(h, b, x, len(probs))
     xs = x.cpu().numpy()
@@ -70,11 +71,11 @@ def test_batch_first_iterates_match_oracle_per_system(s, nu):
     abi.sstep_cg_batch_destroy(h)
 
 
-@pytest.mark.parametrize("use_graph", [0, 1])
-def test_batch_full_solve_matches_oracle_per_system(use_graph):
+@pytest.mark.parametrize("use_graph,gram_form", [(0, "direct"), (1, "direct"), (1, "moments")])
+def test_batch_full_solve_matches_oracle_per_system(use_graph, gram_form):
     from paper_2512_09642_gb300 import abi
     probs = _batch_problems()
-    h, kap, offs, total, lam, b = _make_batch(probs, s=8, nu=20, tol=1e-8, use_graph=use_graph)
+    h, kap, offs, total, lam, b = _make_batch(probs, s=8, nu=20, tol=1e-8, use_graph=use_graph, gram_form=gram_form)
     x = torch.zeros(total, dtype=torch.float64, device="cuda")
     infos, summary = abi.sstep_cg_batch_solve(h, b, x, len(probs))
     assert summary["status"] == "SSTEP_OK", [i["status"] for i in infos]
@@ -90,15 +91,23 @@ def test_batch_full_solve_matches_oracle_per_system(use_graph):
     abi.sstep_cg_batch_destroy(h)
 
 
-def test_batch_graph_equals_host_loop():
+@pytest.mark.parametrize("gram_form", ["direct", "moments"])
+def test_batch_graph_equals_host_loop(gram_form):
     from paper_2512_09642_gb300 import abi
     probs = _batch_problems()
     out = []
     for g in (0, 1):
-        h, kap, offs, total, lam, b = _make_batch(probs, s=8, nu=20, tol=1e-8, use_graph=g)
+        h, kap, offs, total, lam, b = _make_batch(probs, s=8, nu=20, tol=1e-8, use_graph=g, gram_form=gram_form)
         x = torch.zeros(total, dtype=torch.float64, device="cuda")
         infos, _ = abi.sstep_cg_batch_solve(h, b, x, len(probs))
         out.append((x, [i["outer_iters"] for i in infos]))
         abi.sstep_cg_batch_destroy(h)
     assert out[0][1] == out[1][1]
     assert torch.equal(out[0][0], out[1][0])
+
+
+def test_batch_rejects_unsupported_options():
+    from paper_2512_09642_gb300 import abi
+    probs = _batch_problems()[:2]
+    with pytest.raises(abi.SStepError, match="UNSUPPORTED"):
+        _make_batch(probs, s=8, nu=20, precision="mixed")

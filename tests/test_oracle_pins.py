@@ -101,6 +101,64 @@ def test_jacobi_poisson_spectrum_closed_form(dims):
     assert np.allclose(got, np.sort(lam.ravel()), atol=1e-12)
 
 
+@pytest.mark.parametrize("dims", [(7, 5), (5, 4, 3), (3, 1, 2)])
+def test_box_stencil_generator_structure(dims):
+    """27-point (3D) / 9-point (2D) box stencil: diagonal 3^d - 1, -1 for every in-grid point
+    of the unit box; zero row sums inside, positive at the boundary; matrix-free form agrees."""
+    op = O.Operator(*W.box_csr(dims))
+    A = _dense(op)
+    d = len(dims)
+    assert np.array_equal(A, A.T) and np.all(np.diag(A) == 3 ** d - 1)
+    nx, ny, nz = W.grid_shape(dims)
+    idx = np.arange(A.shape[0])
+    i, j, k = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    for r in range(A.shape[0]):
+        nb = [c for c in range(A.shape[0]) if c != r and max(abs(i[c] - i[r]), abs(j[c] - j[r]), abs(k[c] - k[r])) == 1]
+        assert np.all(A[r, nb] == -1) and np.count_nonzero(A[r]) == len(nb) + 1
+    rows = A.sum(axis=1)
+    interior = (i > 0) & (i < nx - 1) & (j > 0) & (j < ny - 1)
+    if d == 3:
+        interior &= (k > 0) & (k < nz - 1)
+    assert np.all(rows[interior] == 0) and np.all(rows[~interior] > 0)
+    x = rng.uniform(7, A.shape[0])
+    assert np.allclose(A @ x, W.box_apply(dims, x), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(8, 6), (5, 4, 3)])
+def test_jacobi_box_stencil_spectrum_closed_form(dims):
+    """A = 3^d I - (T x ... x T) with T = tridiag(1, 1, 1), whose eigenvalues are
+    1 + 2 cos(k pi / (N + 1)); so eig(D^-1 A) = (3^d - prod_i (1 + 2 cos(k_i pi / (N_i + 1)))) / (3^d - 1)."""
+    op = O.Operator(*W.box_csr(dims))
+    got = np.sort(np.linalg.eigvals(np.diag(op.minv) @ _dense(op)).real)
+    d = len(dims)
+    grids = np.meshgrid(*[np.arange(1, N + 1) for N in dims], indexing="ij")
+    prod = np.ones_like(grids[0], dtype=np.float64)
+    for g, N in zip(grids, dims):
+        prod = prod * (1.0 + 2.0 * np.cos(g * np.pi / (N + 1)))
+    lam = (3.0 ** d - prod) / (3.0 ** d - 1)
+    assert np.allclose(got, np.sort(lam.ravel()), atol=1e-12)
+
+
+def test_box_stencil_lanczos_bounds_and_gershgorin():
+    """Gershgorin bounds D^-1 A by 2 while the 27-point spectrum ends near 36/26 (one cosine
+    factor near -1, two near 3), so the paper's Lanczos-10 bounds with their 10% margins
+    enclose the spectrum far more tightly."""
+    dims = (12, 11, 10)
+    op = O.Operator(*W.box_csr(dims))
+    grids = np.meshgrid(*[np.arange(1, N + 1) for N in dims], indexing="ij")
+    prod = np.ones_like(grids[0], dtype=np.float64)
+    for g, N in zip(grids, dims):
+        prod = prod * (1.0 + 2.0 * np.cos(g * np.pi / (N + 1)))
+    lam = (27.0 - prod) / 26.0
+    a, b = OS.lanczos(op, W.lanczos_start(op.n), 10)
+    ev = OS.tridiag_eigvals(a, b)
+    assert lam.min() - 1e-12 <= ev[0] and ev[-1] <= lam.max() + 1e-12
+    assert OS.gershgorin_upper(op) == 2.0 and lam.max() < 36.0 / 26.0
+    lo, hi = OS.bounds(op, "lanczos10", W.lanczos_start(op.n))
+    assert lo == pytest.approx(0.9 * ev[0]) and hi == pytest.approx(1.1 * ev[-1])
+    assert lo < lam.min() and hi > lam.max()
+
+
 def test_diffusion_generator_spd_and_matrix_free_agree():
     dims = (6, 5, 4)
     kappa = W.lognormal_kappa(dims, 1.0, 99)

@@ -7,6 +7,10 @@ Two discretisations on a structured grid with homogeneous Dirichlet boundaries. 
   neighbour that lies inside the grid. This is the 5-point (2D) / 7-point (3D) Laplacian;
   the h**-2 factor is dropped because the relative residual and the Jacobi-preconditioned
   iteration do not depend on it.
+* Box-stencil Poisson (stencil="box"): every one of the 3**dim - 1 grid points of the unit
+  box around a point (faces, edges and corners) is a neighbour with weight -1, and the
+  diagonal is 3**dim - 1: the 27-point finite-difference Laplacian of the paper's experiments
+  (Section 8) in 3D, the 9-point one in 2D, again without the h**-2 factor.
 * Diffusion -div(kappa grad u) (cell-centred finite volumes): an interior face between cells
   a and b has coefficient w = 2 ka kb / (ka + kb) (harmonic mean); it adds w to both
   diagonals and -w to the two off-diagonal entries. A face on the domain boundary (Dirichlet
@@ -155,6 +159,55 @@ def apply(dims, x: np.ndarray, kappa: Optional[np.ndarray] = None) -> np.ndarray
     return Y.reshape(-1)
 
 
+def box_csr(dims, index_dtype=np.int32):
+    """CSR arrays of the box-stencil Poisson matrix (columns ascending in each row)."""
+    nx, ny, nz = grid_shape(dims)
+    d = grid_dim(dims)
+    n = nx * ny * nz
+    rng_z = (-1, 0, 1) if d == 3 else (0,)
+    # offsets (dz, dy, dx) in ascending order of the linear column index
+    offs = [(dz, dy, dx) for dz in rng_z for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    plane = nx * ny
+    slab = max(1, (1 << 21) // plane)
+    counts = np.empty(n, dtype=np.int64)
+    cols_parts, vals_parts = [], []
+    for k0 in range(0, nz, slab):
+        k1 = min(nz, k0 + slab)
+        idx = np.arange(k0 * plane, k1 * plane, dtype=np.int64)
+        ci, cj, ck = idx % nx, (idx // nx) % ny, idx // plane
+        cols = np.empty((idx.size, len(offs)), dtype=np.int64)
+        vals = np.empty((idx.size, len(offs)), dtype=np.float64)
+        valid = np.empty((idx.size, len(offs)), dtype=bool)
+        for slot, (dz, dy, dx) in enumerate(offs):
+            inside = ((ci + dx >= 0) & (ci + dx < nx) & (cj + dy >= 0) & (cj + dy < ny) &
+                      (ck + dz >= 0) & (ck + dz < nz))
+            cols[:, slot] = idx + dx + nx * dy + plane * dz
+            valid[:, slot] = inside
+            vals[:, slot] = float(3 ** d - 1) if (dz, dy, dx) == (0, 0, 0) else -1.0
+        counts[idx] = valid.sum(axis=1)
+        cols_parts.append(cols[valid].astype(index_dtype))
+        vals_parts.append(vals[valid])
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    return rowptr.astype(index_dtype), np.concatenate(cols_parts), np.concatenate(vals_parts)
+
+
+def box_apply(dims, x: np.ndarray) -> np.ndarray:
+    """Matrix-free y = A x of the box-stencil Poisson matrix (used to form b = A x*)."""
+    nx, ny, nz = grid_shape(dims)
+    d = grid_dim(dims)
+    X = np.zeros((nz + 2, ny + 2, nx + 2), dtype=np.result_type(x, np.float64))
+    X[1:-1, 1:-1, 1:-1] = x.reshape(nz, ny, nx)
+    Y = float(3 ** d - 1) * X[1:-1, 1:-1, 1:-1]
+    rng_z = (-1, 0, 1) if d == 3 else (0,)
+    for dz in rng_z:
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if (dz, dy, dx) != (0, 0, 0):
+                    Y = Y - X[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+    return Y.reshape(-1)
+
+
 @dataclass
 class Problem:
     """One synthetic system A x = b with b = A x*, x0 = 0."""
@@ -167,6 +220,7 @@ class Problem:
     nu: int
     tol: float = 1e-8
     meta: dict = field(default_factory=dict)
+    stencil: str = "star"     # "star": 2 dim + 1 points (or diffusion); "box": 3**dim points
 
     @property
     def n(self) -> int:
@@ -174,24 +228,28 @@ class Problem:
         return nx * ny * nz
 
     def csr(self, index_dtype=np.int32):
+        if self.stencil == "box":
+            return box_csr(self.dims, index_dtype)
         return csr(self.dims, self.kappa, index_dtype)
 
 
 def make(name: str, dims, *, kappa_sigma: Optional[float] = None, config: int = 0,
          s: int = 8, nu: int = 25, tol: float = 1e-8, xstar_seed: Optional[int] = None,
-         kappa_seed: Optional[int] = None, **meta) -> Problem:
+         kappa_seed: Optional[int] = None, stencil: str = "star", **meta) -> Problem:
     dims = tuple(int(v) for v in dims)
     nx, ny, nz = grid_shape(dims)
     n = nx * ny * nz
+    if stencil not in ("star", "box") or (stencil == "box" and kappa_sigma is not None):
+        raise ValueError("stencil is 'star' or 'box' (box: Poisson only)")
     kappa = None
     if kappa_sigma is not None:
         kappa = lognormal_kappa(dims, kappa_sigma, SEED_KAPPA + config if kappa_seed is None else kappa_seed)
     xs = rng.uniform(SEED_XSTAR + config if xstar_seed is None else xstar_seed, n)
-    b = apply(dims, xs, kappa)
-    return Problem(name, dims, kappa, xs, b, s, nu, tol, dict(meta, config=config))
+    b = box_apply(dims, xs) if stencil == "box" else apply(dims, xs, kappa)
+    return Problem(name, dims, kappa, xs, b, s, nu, tol, dict(meta, config=config), stencil)
 
 
-# --- the five workloads -------------------------------------------------------------------
+# --- the workloads ------------------------------------------------------------------------
 
 def poisson2d_64() -> Problem:
     """2D 5-point Poisson 64 x 64 (n = 4096), s = 4, nu = 20 (CSR)."""
@@ -206,6 +264,12 @@ def poisson3d(side: int = 256, s: int = 8, nu: int = 25) -> Problem:
 def diffusion3d(side: int = 384, s: int = 12, nu: int = 30, sigma: float = 1.0) -> Problem:
     """3D 7-point variable-coefficient diffusion, log-normal kappa (sigma = 1)."""
     return make(f"diffusion3d_{side}", (side, side, side), kappa_sigma=sigma, config=3, s=s, nu=nu)
+
+
+def poisson27(side: int = 230, s: int = 8, nu: int = 25) -> Problem:
+    """3D 27-point Poisson side**3 (230**3 = 12.2M unknowns, the per-GPU size of the paper's
+    experiments), s = 8, nu = 25."""
+    return make(f"poisson27_{side}", (side, side, side), config=6, s=s, nu=nu, stencil="box")
 
 
 def batch_sides(count: int = 512, lo: int = 32, hi: int = 512, seed: int = SEED_SIDES) -> np.ndarray:
