@@ -442,6 +442,78 @@ def test_lanczos_ritz_values_inside_closed_form_spectrum():
     assert np.allclose(OS.tridiag_eigvals(a, b), np.arange(1.0, 9.0), atol=1e-8)
 
 
+# --- block-conjugated s-step CG (Section 1's Chronopoulos-Gear method) ------------------
+
+def _textbook_cg(A, b, iters):
+    """Unpreconditioned CG by its two-term recurrences (Hestenes-Stiefel), x_0 = 0."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = r @ r
+    out = []
+    for _ in range(iters):
+        Ap = A @ p
+        a = rr / (p @ Ap)
+        x = x + a * p
+        r = r - a * Ap
+        rn = r @ r
+        p = r + (rn / rr) * p
+        rr = rn
+        out.append(x.copy())
+    return out
+
+
+@pytest.mark.parametrize("dims", [(12, 10), (7, 6, 5)])
+@pytest.mark.parametrize("s", [1, 2, 4])
+def test_conjugated_sstep_equals_cg_every_s_steps(dims, s):
+    """With a constant Jacobi diagonal the basis spans K_s(A, r_k); with exact Gram solves the
+    A-conjugate blocks make outer iteration k equal to CG after k s steps (CG's optimality over
+    the Krylov space), so every term of the block recurrence is pinned."""
+    p = W.make("c", dims, config=41)
+    op = O.Operator(*p.csr())
+    lam_min = 0.9 * np.linalg.eigvals(np.diag(op.minv) @ _dense(op)).real.min()
+    res = O.solve_conjugated(op, p.b, s=s, nu=1, lam_min=lam_min, lam_max=2.0, tol=1e-30, max_outer=6,
+                             history=6, gram_solver="cholesky")
+    ref = _textbook_cg(op.A, p.b, 6 * s)
+    for k, h in enumerate(res.history):
+        want = ref[(k + 1) * s - 1]
+        assert np.linalg.norm(h.x - want) <= 1e-12 * np.linalg.norm(want), (k, s)
+
+
+def test_conjugated_s1_with_fgs_equals_cg_on_diffusion():
+    """s = 1: p_0 = r_k, the 1x1 Gram systems are solved exactly by one scaled sweep, so the
+    method is unpreconditioned CG whatever the coefficients (first nine iterations, before
+    finite-precision drift separates the two recurrences)."""
+    p = W.make("c", (12, 10), kappa_sigma=1.0, config=42)
+    op = O.Operator(*p.csr())
+    res = O.solve_conjugated(op, p.b, s=1, nu=1, lam_min=0.01, lam_max=2.0, tol=1e-30, max_outer=9, history=9)
+    ref = _textbook_cg(op.A, p.b, 9)
+    for k, h in enumerate(res.history):
+        assert np.linalg.norm(h.x - ref[k]) <= 1e-11 * np.linalg.norm(ref[k]), k
+
+
+def test_conjugated_fgs_converges_in_fewer_outer_iterations():
+    """With inexact (nu-sweep FGS) Gram solves the conjugated method still reaches tol, in far
+    fewer outer iterations than the restarted iteration of Section 2."""
+    p = W.poisson2d_64()
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+    lit = O.solve(op, p.b, s=4, nu=20, lam_min=lam[0], lam_max=lam[1], tol=1e-8)
+    con = O.solve_conjugated(op, p.b, s=4, nu=20, lam_min=lam[0], lam_max=lam[1], tol=1e-8)
+    assert con.converged and con.rel_res_true < 1e-8
+    assert np.linalg.norm(p.b - op.matvec(con.x)) / np.linalg.norm(p.b) < 1e-8
+    assert con.outer_iters * 3 < lit.outer_iters
+
+
+def test_scaled_solve_with_many_columns_matches_dense_solve():
+    rng_ = np.random.default_rng(3)
+    X = rng_.standard_normal((6, 6))
+    Wm = X @ X.T + 6 * np.eye(6)
+    R = rng_.standard_normal((6, 3))
+    assert np.allclose(O.scaled_solve(Wm, R, 200), np.linalg.solve(Wm, R), rtol=1e-12, atol=1e-12)
+    assert np.allclose(O.scaled_solve(Wm, R, 1, "cholesky"), np.linalg.solve(Wm, R), rtol=1e-12, atol=1e-12)
+
+
 # --- adjoint ----------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dims", [(6, 5), (4, 3, 3)])
