@@ -39,9 +39,9 @@ def parse():
     ap.add_argument("--nu", type=int, default=25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="fp64+mom,mixed+mom,fp64,mixed",
-                    help="comma list of fp64, mixed, fp64+mom, mixed+mom (+mom: Gram from Chebyshev moments); "
-                         "the first is the headline")
+    ap.add_argument("--forms", default="fp64+mom,mixed+mom,fp64,mixed,fp64+mom+conj",
+                    help="comma list of fp64, mixed, fp64+mom, mixed+mom, fp64+mom+conj (+mom: Gram from "
+                         "Chebyshev moments; +conj: block-conjugated s-step CG); the first is the headline")
     ap.add_argument("--graph", action="store_true", help="run the outer loop as one CUDA graph (no kernel sampling)")
     ap.add_argument("--workload", default="poisson3d",
                     choices=["poisson3d", "poisson27", "poisson2d_64", "diffusion3d", "batch"],
@@ -150,7 +150,7 @@ def measured_peaks():
 FP64_OPS_PEAK = 0.625e12
 
 
-def kernel_model(s, mixed=False, dim=3, mom=False, diffusion=False, box=False):
+def kernel_model(s, mixed=False, dim=3, mom=False, diffusion=False, box=False, conj=False):
     """Algorithmic FP64-pipe operations and HBM bytes per unknown per launch of the stencil
     path (change-of-basis Gram; the derivation is in the design notes)."""
     nbr = 2 * dim
@@ -166,9 +166,15 @@ def kernel_model(s, mixed=False, dim=3, mom=False, diffusion=False, box=False):
                           "bytes": 24 + (8 * (dim + 1) if diffusion else 0)},
             # s(s+1)/2 + s FMAs (moments form: 2s), + s for c and s scalings with a vector M;
             # reads the s+1 basis vectors (+ diag M)
-            "gram_fgs": {"ops": gram_fma + (s if diffusion else 0), "bytes": 8 * (s + 1) + (8 if diffusion else 0)},
-            # s FMAs for x, s+1 for r (+1 with a vector M); reads s+1 vectors and x, writes x, r
-            "update": {"ops": 2 * s + 1 + (1 if diffusion else 0), "bytes": 8 * (s + 1) + 24 + (8 if diffusion else 0)},
+            # (+ conj: C = (A Q)^T P and d = Q^T r, s^2 + s FMAs reading P, Q, A Q again)
+            "gram_fgs": {"ops": gram_fma + (s if diffusion else 0) + (s * s + s if conj else 0),
+                         "bytes": 8 * (s + 1) + (8 if diffusion else 0) + (8 * 3 * s if conj else 0)},
+            # s FMAs for x, s+1 for r (+1 with a vector M); reads s+1 vectors and x, writes x, r.
+            # Block-conjugated form: A P through the change of basis (4 s), Q and A Q (2 s^2),
+            # x and r (2 s); reads P_+, Q, A Q, x, writes Q, A Q, x, r
+            "update": ({"ops": 2 * s * s + 6 * s, "bytes": 8 * (s + 1) + 8 * 4 * s + 24 + (8 if diffusion else 0)}
+                       if conj else
+                       {"ops": 2 * s + 1 + (1 if diffusion else 0), "bytes": 8 * (s + 1) + 24 + (8 if diffusion else 0)}),
             # A x, b - A x, the norm FMA; reads x, b (+ faces), writes r
             "residual": {"ops": (box_sum + 3) if box else nbr + 2, "bytes": 24 + (8 * (dim + 1) if diffusion else 0)},
         }
@@ -185,8 +191,8 @@ def kernel_model(s, mixed=False, dim=3, mom=False, diffusion=False, box=False):
     }
 
 
-def outer_bytes(s, mixed=False, dim=3, diffusion=False):
-    m = kernel_model(s, mixed, dim, diffusion=diffusion)
+def outer_bytes(s, mixed=False, dim=3, diffusion=False, conj=False):
+    m = kernel_model(s, mixed, dim, diffusion=diffusion, conj=conj)
     first = 16 if not mixed else 8    # the first step reads no p_(j-1)
     steps = m["cheb_step"]["bytes"] * (s - 1) + first
     extra = m["residual"]["bytes"] if mixed else 0
@@ -281,9 +287,11 @@ def measure_form(args, p, b, world, local, precision, csr=None):
     from paper_2512_09642_gb300 import SStepCG, abi
 
     n, s = p.n, args.s
-    prec, _, form = precision.partition("+")
+    parts = precision.split("+")
+    prec = parts[0]
     kw = dict(s=s, nu=args.nu, tol=1e-8, check_every=8, profile_every=0 if args.graph else 4, precision=prec,
-              gram_form="moments" if form == "mom" else "direct", use_graph=1 if args.graph else 0)
+              gram_form="moments" if "mom" in parts else "direct", use_graph=1 if args.graph else 0,
+              block_conjugate=1 if "conj" in parts else 0)
     if p.stencil == "box":
         kw["bounds_mode"] = "lanczos10"   # Section 8: Lanczos-10 estimates of both ends, 10% margins
     if csr is not None:
@@ -344,11 +352,12 @@ def kernel_report(args, n, infos, precision, dim=3, diffusion=False, box=False):
         per_launch[nm] = tot / cnt if cnt else None
     outers = info["outer_iters"]
     mixed = precision.startswith("mixed")
-    mom = precision.endswith("+mom")
+    mom = "+mom" in precision
+    conj = "+conj" in precision
     launches = {"cheb_step": s * outers, "gram_fgs": outers, "update": outers,
                 "residual": (outers + 1 if mixed else 0) + 2 + info["refreshes"]}
     share = {nm: (per_launch[nm] or 0.0) * launches[nm] for nm in names}
-    model = kernel_model(s, mixed, dim=dim, mom=mom, diffusion=diffusion, box=box)
+    model = kernel_model(s, mixed, dim=dim, mom=mom, diffusion=diffusion, box=box, conj=conj)
     hbm_peak, peak_kind = measured_peaks()
     table = {}
     for nm in names:
@@ -417,11 +426,12 @@ def run_ours(args):
                        else ({}, {}))
         info = r["infos"][-1]
         outers = info["outer_iters"]
-        bytes_solve = outer_bytes(s, prec.startswith("mixed"), dim, diff) * n * outers
+        cj = "+conj" in prec
+        bytes_solve = outer_bytes(s, prec.startswith("mixed"), dim, diff, cj) * n * outers
         forms[prec] = {"time_s": r["t"], "outer_iters": outers, "status": sorted({i["status"] for i in r["infos"]}),
                        "rel_res_true": info["rel_res_true"], "outer_per_s": outers / r["t"],
                        "hbm_gbs_model": bytes_solve / r["t"] / 1e9,
-                       "model_bytes_per_outer": outer_bytes(s, prec.startswith("mixed"), dim, diff) * n,
+                       "model_bytes_per_outer": outer_bytes(s, prec.startswith("mixed"), dim, diff, cj) * n,
                        "e2e_s": r["e2e"], "roofline": roof, "kernels": table, "clocks": r["clocks"],
                        "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"]))}
         res[prec] = r

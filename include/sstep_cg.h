@@ -85,6 +85,12 @@ typedef struct {
                               check intervals with CUDA events (sstep_cg_info.prof_*); 0: off */
     int batch_chunk;       /* batched form: unknowns per Gram/update work item (0: 8192) */
     int batch_ctas_per_sm; /* batched form: resident blocks per SM of the stencil kernels (0: 6) */
+    int block_conjugate;   /* 1: make each Chebyshev block A-conjugate to the previous one (the
+                              Chronopoulos-Gear s-step CG cited in Section 1): Q_k = P_k -
+                              Q_(k-1) W_(k-1)^-1 (A Q_(k-1))^T P_k, x += Q_k alpha; B is solved
+                              with the same scaled FGS as alpha. FP64, s <= 16 (else
+                              SSTEP_ERR_UNSUPPORTED); 2s more basis-length vectors of workspace.
+                              0 (default): the restarted iteration of Section 2 as written */
 } sstep_cg_opts;
 
 typedef struct {

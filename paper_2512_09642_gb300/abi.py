@@ -30,7 +30,7 @@ class Opts(C.Structure):
                 ("precision", C.c_int), ("precond", C.c_int), ("basis_start", C.c_int), ("gram_form", C.c_int),
                 ("refresh_period", C.c_int), ("max_refresh", C.c_int), ("seed", C.c_uint64),
                 ("use_graph", C.c_int), ("check_every", C.c_int), ("profile_every", C.c_int),
-                ("batch_chunk", C.c_int), ("batch_ctas_per_sm", C.c_int)]
+                ("batch_chunk", C.c_int), ("batch_ctas_per_sm", C.c_int), ("block_conjugate", C.c_int)]
 
 
 class Info(C.Structure):

@@ -34,6 +34,10 @@ struct sstep_cg_s {
     double* gram_partials = nullptr;
     int gram_nblk = 0;
     double* res_partials = nullptr;
+    bool conj = false;          // block-conjugated form: P holds P_+, Q_(k-1), A Q_(k-1)
+    double* conj_partials = nullptr;
+    int conj_nblk = 0;
+    double* cj = nullptr;       // [W_(k-1) | B_k], s x s each
     Ctl* ctl = nullptr;
     Ctl* ctl_h = nullptr;       // pinned mirror
     double* bx_dev = nullptr;   // device b, x for sstep_cg_solve_host
@@ -98,6 +102,14 @@ sstep_status validate_opts(sstep_cg_t h, const sstep_cg_opts* o) {
         return SSTEP_ERR_INVALID_ARG;
     }
     if (o->refresh_period < 1) { set_err(h, "refresh_period < 1"); return SSTEP_ERR_INVALID_ARG; }
+    if (o->block_conjugate != 0 && o->block_conjugate != 1) {
+        set_err(h, "block_conjugate must be 0 or 1");
+        return SSTEP_ERR_INVALID_ARG;
+    }
+    if (o->block_conjugate && (o->precision != SSTEP_PRECISION_FP64 || o->s > 16)) {
+        set_err(h, "block_conjugate needs FP64 and s <= 16");
+        return SSTEP_ERR_UNSUPPORTED;
+    }
     if (o->precision == SSTEP_PRECISION_MIXED && o->refresh_period != 1) {
         set_err(h, "mixed precision refreshes r = b - A x every outer iteration (refresh_period 1)");
         return SSTEP_ERR_UNSUPPORTED;
@@ -323,6 +335,18 @@ GramArgs gram_args(sstep_cg_t h) {
     return g;
 }
 
+// The same, with the block-conjugated form's inputs (used by the outer iteration only).
+GramArgs gram_args_outer(sstep_cg_t h) {
+    GramArgs g = gram_args(h);
+    if (h->conj) {
+        g.conj = 1;
+        g.conj_nblk = h->conj_nblk;
+        g.conj_partials = h->conj_partials;
+        g.cj = h->cj;
+    }
+    return g;
+}
+
 // FP32 copies of the operator for the mixed form's basis (rounded to nearest).
 sstep_status make_f32_operator(sstep_cg_t h) {
     const int64_t n = h->op.n;
@@ -362,7 +386,15 @@ sstep_status finish_create(sstep_cg_t h) {
         h->op.cdinv = h->cdinv;
     }
     h->ld = (n + 31) / 32 * 32;
-    CK(cudaMalloc(&h->P, sizeof(double) * h->ld * (h->opts.s + 1)));
+    // P_+ (s+1 columns); the conjugated form adds Q_(k-1) and A Q_(k-1) (s columns each)
+    const int ncols = h->conj ? 3 * h->opts.s + 1 : h->opts.s + 1;
+    CK(cudaMalloc(&h->P, sizeof(double) * h->ld * ncols));
+    if (h->conj) {
+        const int s = h->opts.s;
+        h->conj_nblk = conj_cd_blocks(s, n, h->sm_count);
+        CK(cudaMalloc(&h->conj_partials, sizeof(double) * (size_t)h->conj_nblk * (s * s + s)));
+        CK(cudaMalloc(&h->cj, sizeof(double) * 2 * s * s));
+    }
     if (h->mixed) {
         CK(cudaMalloc(&h->P32, sizeof(float) * h->ld * (h->opts.s + 1)));
         if ((st = make_f32_operator(h)) != SSTEP_OK) return st;
@@ -394,6 +426,7 @@ sstep_status begin_create(sstep_cg_t* out, const sstep_cg_opts* opts, void* stre
     h->stream = (cudaStream_t)stream;
     h->jacobi = o.precond == SSTEP_PRECOND_JACOBI;
     h->mixed = o.precision == SSTEP_PRECISION_MIXED;
+    h->conj = o.block_conjugate != 0;
     return SSTEP_OK;
 }
 
@@ -440,11 +473,16 @@ sstep_status launch_outer(sstep_cg_t h, const double* b, double* x, int* launche
         }
         if (prof) CK(cudaEventRecord(h->ev[ev++], h->stream));
     }
-    GramArgs g = gram_args(h);
+    GramArgs g = gram_args_outer(h);
+    if (h->conj)   // C and d for the block conjugation (timed with the Gram)
+        CK(launch_conj_cd(s, h->P, h->ld, h->op.n, h->conj_partials, h->conj_nblk, h->ctl, h->stream));
     CK(launch_gram(g, h->gram_partials, h->ctl, h->gram_nblk, h->stream));
     if (prof) CK(cudaEventRecord(h->ev[ev++], h->stream));
     if (h->mixed) {
         CK(launch_update_mixed(h->P32, h->ld, s, h->op.n, x, h->ctl, h->stream));
+    } else if (h->conj) {
+        CK(launch_update_conj(s, h->P, h->ld, h->op.n, g.dvec ? h->diag : nullptr, g.dconst, h->theta, h->sigma,
+                              h->cj, x, h->ctl, h->stream));
     } else {
         UpdateArgs u{};
         u.s = s;
@@ -459,7 +497,7 @@ sstep_status launch_outer(sstep_cg_t h, const double* b, double* x, int* launche
         CK(launch_update(u, h->ctl, h->stream));
     }
     if (prof) CK(cudaEventRecord(h->ev[ev++], h->stream));
-    *launches += s + 2 + (h->mixed ? 1 : 0);
+    *launches += s + 2 + (h->mixed ? 1 : 0) + (h->conj ? 1 : 0);
     return SSTEP_OK;
 }
 
@@ -590,7 +628,11 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
     ++launches;
     sstep_status status = SSTEP_OK;
     int refreshes = 0;
-    const int outer_launches = h->opts.s + 2 + (h->mixed ? 1 : 0);
+    const int outer_launches = h->opts.s + 2 + (h->mixed ? 1 : 0) + (h->conj ? 1 : 0);
+    // conjugated form: the first block has no predecessor (Q_(-1) = A Q_(-1) = 0)
+    if (h->conj)
+        CK(cudaMemsetAsync(h->P + (int64_t)(h->opts.s + 1) * h->ld, 0, sizeof(double) * 2 * h->opts.s * h->ld,
+                           h->stream));
     for (long chunk = 0;; ++chunk) {
         if (h->opts.use_graph) {
             if (!h->gexec || h->g_b != b || h->g_x != x)
@@ -602,10 +644,17 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
             launches += (h->ctl_h->outer - before + 1) * (outer_launches + 1);
         } else {
             const bool prof = profiling && chunk % h->opts.profile_every == 0;
+            // the sampled outer iteration is the chunk's second (the very first outer iteration
+            // of a solve is not typical: in the conjugated form its previous block is zero)
+            const int sample = h->opts.check_every > 1 ? 1 : 0;
+            const int before = h->ctl_h->outer;
             for (int m = 0; m < h->opts.check_every; ++m)
-                if ((st = launch_outer(h, b, x, &launches, prof && m == 0)) != SSTEP_OK) return st;
+                if ((st = launch_outer(h, b, x, &launches, prof && m == sample)) != SSTEP_OK) return st;
             if ((st = read_ctl(h)) != SSTEP_OK) return st;
-            if (prof && (st = collect_outer_profile(h, &inf)) != SSTEP_OK) return st;
+            // keep the sample only if that outer iteration did its work (its kernels exit at once
+            // after convergence)
+            if (prof && h->ctl_h->outer > before + sample && (st = collect_outer_profile(h, &inf)) != SSTEP_OK)
+                return st;
         }
         const int done = h->ctl_h->done;
         if (done == RUNNING) continue;
@@ -620,6 +669,8 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
             CK(cudaMemcpyAsync(h->P, h->rtrue, sizeof(double) * h->op.n, cudaMemcpyDeviceToDevice, h->stream));
             const int zero = RUNNING;
             CK(cudaMemcpyAsync(&h->ctl->done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+            // a replaced residual restarts the block conjugation (the next block is Q = P)
+            if (h->conj) CK(cudaMemcpyAsync(&h->ctl->conj_valid, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
             CK(cudaStreamSynchronize(h->stream));
             continue;
         }
@@ -682,6 +733,7 @@ void sstep_cg_default_opts(sstep_cg_opts* o) {
     o->profile_every = 0;
     o->batch_chunk = 0;
     o->batch_ctas_per_sm = 0;
+    o->block_conjugate = 0;
 }
 
 sstep_status sstep_cg_create_csr(sstep_cg_t* out, int64_t n, const int32_t* rowptr_d, const int32_t* colind_d,
@@ -839,6 +891,8 @@ sstep_status sstep_cg_destroy(sstep_cg_t h) {
     cudaFree(h->rtrue);
     cudaFree(h->gram_partials);
     cudaFree(h->res_partials);
+    cudaFree(h->conj_partials);
+    cudaFree(h->cj);
     cudaFree(h->ctl);
     cudaFree(h->bx_dev);
     drop_graph(h);

@@ -179,6 +179,7 @@ sstep_status sstep_cg_batch_create(sstep_cg_batch_t* out, int count, const int* 
         return fail(SSTEP_ERR_INVALID_ARG);
     }
     if (o.precond != SSTEP_PRECOND_JACOBI || o.precision != SSTEP_PRECISION_FP64 || o.basis_start != SSTEP_START_R ||
+        o.block_conjugate != 0 ||
         (o.gram_form != SSTEP_GRAM_FORM_DIRECT && o.gram_form != SSTEP_GRAM_FORM_MOMENTS)) {
         berr(h, "batched form: Jacobi, FP64 and p_0 = r only");
         return fail(SSTEP_ERR_UNSUPPORTED);

@@ -33,6 +33,7 @@ struct Ctl {
     double scale;             // mixed form: power of two applied to p_0 in this outer iteration
     double scale_next;        // mixed form: power of two the next refresh applies
     int done;
+    int conj_valid;           // block-conjugated form: 1 once a previous block (W, Q, AQ) exists
     int outer;                // outer iterations applied
     int max_outer;
     int launches;             // not maintained on device; reserved

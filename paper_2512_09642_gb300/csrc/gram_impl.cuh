@@ -198,12 +198,168 @@ struct GramParams {
     int check;                   // 1: convergence / max-outer test on c_0 = ||r_k||^2 (FP64 form);
                                  // 0: done by the FP64 residual refresh (mixed form)
     double theta, sigma, dfac;   // dfac: constant diagonal of M (1 when M = I); unused if DV
+    // block-conjugated form (conj = 1): per-block partials of C = (A Q_(k-1))^T P_k and
+    // d = Q_(k-1)^T r_k from k_conj_cd, and the state cj = [W_(k-1) | B_k] (row-major s x s each)
+    int conj, conj_nblk;
+    const double* conj_partials;
+    double* cj;
 };
+
+// nu forward Gauss-Seidel sweeps on one right-hand side, lane j owning row j (lanes >= S and
+// rows whose bit is clear in `kept` hold 0): grow = row `lane` of the scaled matrix divided by
+// its diagonal, chat = the scaled right-hand side over the same diagonal. A sweep is S
+// warp-wide steps: step i broadcasts the new a_i; rows below i take its product into this
+// sweep's accumulator u (new values, lower triangle), rows above into the next sweep's v
+// (old values, upper triangle). Returns a_lane.
+template <int S>
+__device__ __forceinline__ double fgs_lane(const double (&grow)[S], double chat, unsigned kept, int nu) {
+    const int lane = threadIdx.x & 31;
+    double a = 0.0;
+    double u = chat, v = chat;
+    for (int sweep = 0; sweep < nu; ++sweep) {
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            double ai = __shfl_sync(0xffffffffu, u, i);
+            if (!((kept >> i) & 1u)) ai = 0.0;
+            if (lane == i) a = ai;
+            double w = lane > i ? u : v;
+            w = fma(-grow[i], ai, w);
+            if (lane > i) u = w;
+            else if (lane < i) v = w;
+        }
+        u = v;
+        v = chat;
+    }
+    return a;
+}
+
+// Block conjugation (the Chronopoulos-Gear s-step CG cited in Section 1), applied to the
+// s x s quantities of outer iteration k before its Gram solve (warp 0). With Q_k = P_k -
+// Q_(k-1) B_k, B_k = W_(k-1)^-1 C, C = (A Q_(k-1))^T P_k:
+//   W_k = Q_k^T A Q_k = G - C^T B - B^T C + B^T W_(k-1) B,   g = Q_k^T r_k = c - B^T d,
+// with G = P_k^T A P_k, c = P_k^T r_k and d = Q_(k-1)^T r_k. B is solved column by column
+// with the same column scaling and nu FGS sweeps as the Gram system. Gs / cs hold G and c on
+// entry and W_k and g on exit; cj receives W_k and B for the next iteration and the update.
+// scr: >= 3 S^2 + S doubles. The first block (conj_valid = 0) has Q = P, B = 0.
+template <int S>
+__device__ void conj_transform(double* Gs, double* cs, const double* totc, const GramParams& gp, Ctl* ctl,
+                               double* scr) {
+    const int lane = threadIdx.x;
+    double* B = scr;
+    double* T = scr + S * S;
+    double* Wp = scr + 2 * S * S;
+    double* dw = scr + 3 * S * S;
+    const double* C = totc;            // C[i * S + j] = (A q_i)^T p_j
+    const double* dq = totc + S * S;   // d[i] = q_i^T r
+    const bool valid = ctl->conj_valid != 0;
+    if (!valid) {
+        for (int idx = lane; idx < S * S; idx += 32) B[idx] = 0.0;
+        __syncwarp();
+    } else {
+        for (int idx = lane; idx < S * S; idx += 32) Wp[idx] = gp.cj[idx];
+        __syncwarp();
+        const double gjj = lane < S ? Wp[lane * S + lane] : 0.0;
+        const bool keep = lane < S && gjj > 0.0 && isfinite(gjj);
+        const double dj = keep ? 1.0 / sqrt(gjj) : 0.0;
+        if (lane < S) dw[lane] = dj;
+        const unsigned kept = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (gp.solver == SSTEP_GRAM_SOLVE_FGS) {
+            const double gd = keep ? dj * gjj * dj : 1.0;
+            const double inv = keep ? 1.0 / gd : 0.0;
+            double grow[S];
+#pragma unroll
+            for (int i = 0; i < S; ++i) grow[i] = lane < S ? dj * Wp[lane * S + i] * dw[i] * inv : 0.0;
+            for (int j = 0; j < S; ++j) {
+                const double chat = lane < S ? dj * C[lane * S + j] * inv : 0.0;
+                const double a = fgs_lane<S>(grow, chat, kept, gp.nu);
+                if (lane < S) B[lane * S + j] = dj * a;
+            }
+        } else if (lane == 0) {
+            // Cholesky of the scaled kept block of W_(k-1) (R in T's storage), then the S columns
+            double* R = T;
+            bool ok = true;
+            for (int j = 0; j < S && ok; ++j) {
+                if (!((kept >> j) & 1u)) continue;
+                double accd = dw[j] * Wp[j * S + j] * dw[j];
+                for (int k = 0; k < j; ++k)
+                    if ((kept >> k) & 1u) accd -= R[k * S + j] * R[k * S + j];
+                if (!(accd > 0.0)) { ok = false; break; }
+                R[j * S + j] = sqrt(accd);
+                for (int i = j + 1; i < S; ++i) {
+                    if (!((kept >> i) & 1u)) continue;
+                    double v = dw[j] * Wp[j * S + i] * dw[i];
+                    for (int k = 0; k < j; ++k)
+                        if ((kept >> k) & 1u) v -= R[k * S + j] * R[k * S + i];
+                    R[j * S + i] = v / R[j * S + j];
+                }
+            }
+            for (int col = 0; col < S; ++col) {
+                double y[S], a[S];
+                for (int i = 0; i < S; ++i) {
+                    y[i] = 0.0;
+                    if (!ok || !((kept >> i) & 1u)) continue;
+                    double v = dw[i] * C[i * S + col];
+                    for (int k = 0; k < i; ++k)
+                        if ((kept >> k) & 1u) v -= R[k * S + i] * y[k];
+                    y[i] = v / R[i * S + i];
+                }
+                for (int i = S - 1; i >= 0; --i) {
+                    a[i] = 0.0;
+                    if (!ok || !((kept >> i) & 1u)) continue;
+                    double v = y[i];
+                    for (int k = i + 1; k < S; ++k)
+                        if ((kept >> k) & 1u) v -= R[i * S + k] * a[k];
+                    a[i] = v / R[i * S + i];
+                }
+                for (int i = 0; i < S; ++i) B[i * S + col] = dw[i] * a[i];
+            }
+            if (!ok) ctl->done = NUMERICAL;
+        }
+        __syncwarp();
+        if (ctl->done != RUNNING) return;
+        // T = W_(k-1) B
+        for (int idx = lane; idx < S * S; idx += 32) {
+            const int i = idx / S, b = idx % S;
+            double v = 0.0;
+            for (int k = 0; k < S; ++k) v = fma(Wp[i * S + k], B[k * S + b], v);
+            T[idx] = v;
+        }
+        __syncwarp();
+        // W_k from its lower triangle, mirrored
+        for (int idx = lane; idx < S * S; idx += 32) {
+            const int a = idx / S, b = idx % S;
+            if (a < b) continue;
+            double w = Gs[a * S + b];
+            for (int i = 0; i < S; ++i) {
+                w = fma(-C[i * S + a], B[i * S + b], w);
+                w = fma(-B[i * S + a], C[i * S + b], w);
+                w = fma(B[i * S + a], T[i * S + b], w);
+            }
+            Gs[a * S + b] = w;
+            Gs[b * S + a] = w;
+        }
+        double g = 0.0;
+        if (lane < S) {
+            g = cs[lane];
+            for (int i = 0; i < S; ++i) g = fma(-B[i * S + lane], dq[i], g);
+        }
+        __syncwarp();
+        if (lane < S) cs[lane] = g;
+        __syncwarp();
+    }
+    for (int idx = lane; idx < S * S; idx += 32) {
+        gp.cj[idx] = Gs[idx];
+        gp.cj[S * S + idx] = B[idx];
+    }
+    __syncwarp();
+}
 
 // The s x s work of one outer iteration, executed by warp 0 of the last block.
 // tot[]: reduced entries (layout of gram_entry). Writes ctl.
 template <int S, bool DV, bool MOM = false>
-__device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, double* sm /* >= 2*S*S + 4*S doubles */) {
+__device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, double* sm /* >= 2*S*S + 4*S doubles */,
+                            const double* totc = nullptr, double* cscr = nullptr) {
     const int lane = threadIdx.x;   // warp 0 only
     constexpr int NSYM = S * (S + 1) / 2;
     constexpr int NW = MOM ? 2 * S : NSYM + S;   // where the unweighted c entries start
@@ -260,6 +416,13 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     }
     __syncwarp();
     if (ctl->done != RUNNING) return;
+    if constexpr (S <= 16) {
+        if (totc) {
+            conj_transform<S>(Gs, cs, totc, gp, ctl, cscr);
+            __syncwarp();
+            if (ctl->done != RUNNING) return;
+        }
+    }
     // column scaling (Section 2, "Column scaling")
     double gjj = lane < S ? Gs[lane * S + lane] : 0.0;
     const bool keep = lane < S && gjj > 0.0 && isfinite(gjj);
@@ -292,21 +455,7 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
 #pragma unroll
         for (int i = 0; i < S; ++i) grow[i] = lane < S ? Gs[lane * S + i] * inv : 0.0;
         const double chat = lane < S ? cs[lane] * inv : 0.0;
-        double u = chat, v = chat;
-        for (int sweep = 0; sweep < gp.nu; ++sweep) {
-#pragma unroll
-            for (int i = 0; i < S; ++i) {
-                double ai = __shfl_sync(0xffffffffu, u, i);
-                if (!((kept >> i) & 1u)) ai = 0.0;
-                if (lane == i) a = ai;
-                double w = lane > i ? u : v;
-                w = fma(-grow[i], ai, w);
-                if (lane > i) u = w;
-                else if (lane < i) v = w;
-            }
-            u = v;
-            v = chat;
-        }
+        a = fgs_lane<S>(grow, chat, kept, gp.nu);
     } else {
         // Cholesky of the kept block of G~ (lane 0, sequential), the O(s^3) baseline.
         double* R = sm + S * S + 4 * S;   // S*S scratch
@@ -387,6 +536,7 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     if (lane == 0) {
         ctl->delta = cn > 0.0 ? sqrt(res / cn) : 0.0;
         ctl->outer += 1;
+        if (totc) ctl->conj_valid = 1;
     }
 }
 
@@ -428,9 +578,26 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram(const T* __restrict__ 
         v = warp_sum(v);
         if (lane == 0) tot[k] = v;
     }
+    // block-conjugated form (FP64, S <= 16): the C and d partials of k_conj_cd, summed in block
+    // order like the Gram's
+    constexpr bool CJ = !F32 && S <= 16;
+    constexpr int MC = CJ ? S * S + S : 1;
+    __shared__ double totc[MC];
+    __shared__ double cscr[CJ ? 3 * S * S + S : 1];
+    if (CJ && gp.conj) {
+        for (int k = warp; k < MC; k += GRAM_WARPS) {
+            double v = 0.0;
+            for (int b = lane; b < gp.conj_nblk; b += 32) v += gp.conj_partials[(size_t)b * MC + k];
+            v = warp_sum(v);
+            if (lane == 0) totc[k] = v;
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) ctl->counter = 0u;
-    if (warp == 0) gram_finish<S, DV, MOM>(tot, gp, ctl, smem);
+    if (warp == 0) {
+        if (CJ && gp.conj) gram_finish<S, DV, MOM>(tot, gp, ctl, smem, totc, cscr);
+        else gram_finish<S, DV, MOM>(tot, gp, ctl, smem);
+    }
 }
 
 // Resident blocks per SM of the kernel variant g selects (for sizing the grid).
@@ -453,13 +620,17 @@ int gram_occupancy_s(const GramArgs& g) {
 
 template <int S>
 cudaError_t launch_gram_s(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st) {
-    GramParams gp;
+    GramParams gp{};
     gp.nu = g.nu;
     gp.solver = g.solver;
     gp.check = g.fp32 ? 0 : 1;
     gp.theta = g.theta;
     gp.sigma = g.sigma;
     gp.dfac = g.dconst;
+    gp.conj = g.conj;
+    gp.conj_nblk = g.conj_nblk;
+    gp.conj_partials = g.conj_partials;
+    gp.cj = g.cj;
     const bool mom = g.form == SSTEP_GRAM_FORM_MOMENTS;
 #define SSTEP_GRAM_LAUNCH(DV, T, MOM, DIAG) \
     k_gram<S, DV, T, MOM><<<nblocks, GRAM_THREADS, 0, st>>>((const T*)g.P, g.ld, DIAG, g.n, partials, ctl, gp)

@@ -24,6 +24,9 @@ constexpr int RB = 256;                      // CSR / vector kernels: threads pe
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+inline bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
 // Face weights of the diffusion stencil in precision T.
 template <typename T> struct Faces { const T* wx; const T* wy; const T* wz; const T* diag; const T* cdinv; };
 
@@ -85,6 +88,63 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_stencil(const T* __restrict__ p
             }
         }
         out[e] = o;
+        pdn = pc;
+        pc = pup;
+    }
+}
+
+// Poisson step with each thread on two x-adjacent points (nx even): 16-byte (8-byte in FP32)
+// loads and stores of the pair, the x-neighbours from the adjacent lanes by warp shuffles
+// (the warp's two edge points from memory), so a point costs 3 load instructions instead of
+// 6 (the single-point kernel saturates the load pipe before the FP64 pipe). Same sums in the
+// same order as k_cheb_stencil.
+template <typename T> struct Pair;
+template <> struct Pair<double> { using type = double2; };
+template <> struct Pair<float> { using type = float2; };
+
+template <typename T, int DIM, bool FIRST>
+__global__ void __launch_bounds__(BX* BY) k_cheb_poisson_pair(const T* __restrict__ p, const T* __restrict__ q,
+                                                              T* __restrict__ out, int nx, int ny, int nz, T c1, T c2,
+                                                              const Ctl* __restrict__ ctl) {
+    if (ctl->done) return;
+    using V = typename Pair<T>::type;
+    const int lane = threadIdx.x;   // BX = 32: one warp per row of the tile
+    const int i0 = blockIdx.x * (2 * BX);
+    const int i = i0 + 2 * lane;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const bool in = i < nx && j < ny;   // nx even: i + 1 < nx as well
+    const int64_t sxy = (int64_t)nx * ny;
+    const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
+    const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+    const int64_t ij = in ? i + (int64_t)nx * j : 0;
+    const V zero{T(0), T(0)};
+    auto ld2 = [&](int64_t e) { return __ldg(reinterpret_cast<const V*>(p + e)); };
+    V pdn = (DIM == 3 && in && k0 > 0) ? ld2(ij + sxy * (k0 - 1)) : zero;
+    V pc = in ? ld2(ij + sxy * k0) : zero;
+    for (int k = k0; k < k1; ++k) {
+        const int64_t e = ij + sxy * k;
+        const V pup = (DIM == 3 && in && k < nz - 1) ? ld2(e + sxy) : zero;
+        const V ym = (in && j > 0) ? ld2(e - nx) : zero;
+        const V yp = (in && j < ny - 1) ? ld2(e + nx) : zero;
+        const V qv = (FIRST || !in) ? zero : __ldg(reinterpret_cast<const V*>(q + e));
+        // left of the pair: the lane below's right point; right of the pair: the lane above's
+        // left point (0 from lanes outside the grid, which is the Dirichlet value there)
+        T xl = __shfl_up_sync(0xffffffffu, pc.y, 1);
+        T xr = __shfl_down_sync(0xffffffffu, pc.x, 1);
+        if (lane == 0) xl = (in && i0 > 0) ? ldg(p + e - 1) : T(0);
+        if (lane == BX - 1) xr = (in && i + 2 < nx) ? ldg(p + e + 2) : T(0);
+        if (in) {
+            T s0 = (xl + pc.y) + (ym.x + yp.x);
+            T s1 = (pc.x + xr) + (ym.y + yp.y);
+            if (DIM == 3) {
+                s0 += pdn.x + pup.x;
+                s1 += pdn.y + pup.y;
+            }
+            V o;
+            o.x = FIRST ? fma(c2, s0, c1 * pc.x) : fma(c2, s0, fma(c1, pc.x, -qv.x));
+            o.y = FIRST ? fma(c2, s1, c1 * pc.y) : fma(c2, s1, fma(c1, pc.y, -qv.y));
+            *reinterpret_cast<V*>(out + e) = o;
+        }
         pdn = pc;
         pc = pup;
     }
@@ -239,6 +299,73 @@ __global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __res
     double tot = 0.0;
     if (t == 0)
         for (int k = 0; k < BX * BY / 32; ++k) tot += sh[k];
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, nblk);
+}
+
+// r = b - A x for the Poisson stencil with each thread on two x-adjacent points (nx even), as
+// k_cheb_poisson_pair; sums in the same order as k_residual_stencil.
+template <int DIM>
+__global__ void __launch_bounds__(BX* BY) k_residual_poisson_pair(const double* __restrict__ b,
+                                                                  const double* __restrict__ x, double* __restrict__ r,
+                                                                  float* __restrict__ r32, int nx, int ny, int nz,
+                                                                  double d2, double* partials, Ctl* ctl, int mode) {
+    if (mode == 2 && ctl->done) return;
+    int kscale = 0;   // scale_next = 2^kscale
+    if (mode == 2) {
+        frexp(ctl->scale_next, &kscale);
+        kscale -= 1;
+    }
+    const int lane = threadIdx.x;
+    const int i0 = blockIdx.x * (2 * BX);
+    const int i = i0 + 2 * lane;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const bool in = i < nx && j < ny;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
+    const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+    const int64_t ij = in ? i + (int64_t)nx * j : 0;
+    const double2 zero{0.0, 0.0};
+    auto ld2 = [&](const double* a, int64_t e) { return __ldg(reinterpret_cast<const double2*>(a + e)); };
+    double2 pdn = (DIM == 3 && in && k0 > 0) ? ld2(x, ij + sxy * (k0 - 1)) : zero;
+    double2 pc = in ? ld2(x, ij + sxy * k0) : zero;
+    double ss = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const int64_t e = ij + sxy * k;
+        const double2 pup = (DIM == 3 && in && k < nz - 1) ? ld2(x, e + sxy) : zero;
+        const double2 ym = (in && j > 0) ? ld2(x, e - nx) : zero;
+        const double2 yp = (in && j < ny - 1) ? ld2(x, e + nx) : zero;
+        const double2 bv = in ? ld2(b, e) : zero;
+        double xl = __shfl_up_sync(0xffffffffu, pc.y, 1);
+        double xr = __shfl_down_sync(0xffffffffu, pc.x, 1);
+        if (lane == 0) xl = (in && i0 > 0) ? ldg(x + e - 1) : 0.0;
+        if (lane == BX - 1) xr = (in && i + 2 < nx) ? ldg(x + e + 2) : 0.0;
+        if (in) {
+            double s0 = ((xl + pc.y) + ym.x) + yp.x;
+            double s1 = ((pc.x + xr) + ym.y) + yp.y;
+            if (DIM == 3) {
+                s0 = (s0 + pdn.x) + pup.x;
+                s1 = (s1 + pdn.y) + pup.y;
+            }
+            double2 rv;
+            rv.x = bv.x - fma(d2, pc.x, -s0);
+            rv.y = bv.y - fma(d2, pc.y, -s1);
+            if (r) *reinterpret_cast<double2*>(r + e) = rv;
+            if (r32) *reinterpret_cast<float2*>(r32 + e) = make_float2(d2f_scaled(rv.x, kscale), d2f_scaled(rv.y, kscale));
+            ss = fma(rv.x, rv.x, ss);
+            ss = fma(rv.y, rv.y, ss);
+        }
+        pdn = pc;
+        pc = pup;
+    }
+    __shared__ double sh[BX * BY / 32];
+    double v = warp_sum(ss);
+    const int t = threadIdx.x + BX * threadIdx.y;
+    if ((t & 31) == 0) sh[t >> 5] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (t == 0)
+        for (int kk = 0; kk < BX * BY / 32; ++kk) tot += sh[kk];
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, nblk);
 }
@@ -406,6 +533,49 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_box(const T* __restrict__ p, co
         });
 }
 
+// FP32 box step (mixed form): the FP32 pipe has room for the plain 3 x 3 in-plane sums (9
+// loads through L1 and 8 adds per point and plane, the z-window of plane sums in registers),
+// which needs no shared memory and no barriers, so the kernel can run at the HBM rate.
+template <int DIM, bool FIRST>
+__global__ void __launch_bounds__(BX* BY) k_cheb_box_f32(const float* __restrict__ p, const float* __restrict__ q,
+                                                         float* __restrict__ out, int nx, int ny, int nz, float ca,
+                                                         float cb, const Ctl* __restrict__ ctl) {
+    if (ctl->done) return;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const int64_t sxy = (int64_t)nx * ny, ij = i + (int64_t)nx * j;
+    const bool xm = i > 0, xp = i < nx - 1, ym = j > 0, yp = j < ny - 1;
+    auto row = [&](const float* a) { return ((xm ? ldg(a - 1) : 0.f) + ldg(a)) + (xp ? ldg(a + 1) : 0.f); };
+    auto plane = [&](int k, float& center) {   // 3 x 3 sum of plane k around (i, j)
+        const float* a = p + sxy * k + ij;
+        center = ldg(a);
+        const float r0 = ym ? row(a - nx) : 0.f;
+        const float r1 = ((xm ? ldg(a - 1) : 0.f) + center) + (xp ? ldg(a + 1) : 0.f);
+        const float r2 = yp ? row(a + nx) : 0.f;
+        return (r0 + r1) + r2;
+    };
+    if (DIM == 2) {
+        float pc;
+        const float S = plane(0, pc);
+        out[ij] = FIRST ? fmaf(cb, S, ca * pc) : fmaf(cb, S, fmaf(ca, pc, -ldg(q + ij)));
+        return;
+    }
+    const int k0 = blockIdx.z * KB, k1 = min(nz, k0 + KB);
+    float pc, ptmp;
+    float sdn = (k0 > 0) ? plane(k0 - 1, ptmp) : 0.f;
+    float sc = plane(k0, pc);
+    for (int k = k0; k < k1; ++k) {
+        float pup = 0.f, sup = 0.f;
+        if (k + 1 < nz) sup = plane(k + 1, pup);
+        const int64_t e = ij + sxy * k;
+        const float B = (sdn + sc) + sup;
+        out[e] = FIRST ? fmaf(cb, B, ca * pc) : fmaf(cb, B, fmaf(ca, pc, -ldg(q + e)));
+        sdn = sc;
+        sc = sup;
+        pc = pup;
+    }
+}
+
 // r = b - A x = b - (3^d x - B) with ||r||^2 (residual modes as k_residual_stencil).
 template <int DIM>
 __global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restrict__ b, const double* __restrict__ x,
@@ -503,6 +673,18 @@ void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, dou
         const double d2 = 2.0 * op.dim;
         const double c1 = jacobi ? c * (1.0 - sigma) : c * (d2 - sigma);
         const double c2 = jacobi ? -c / d2 : -c;
+        // pair kernel: with nx even every pair starts at an even index, so its 2-element loads
+        // and stores are aligned when the columns are (the workspace's always are)
+        const size_t al = 2 * sizeof(T);
+        const bool aligned = ((uintptr_t)p % al == 0) && ((uintptr_t)out % al == 0) && (!q || (uintptr_t)q % al == 0);
+        if (op.nx % 2 == 0 && aligned) {
+            const dim3 g2((op.nx + 2 * BX - 1) / (2 * BX), grid.y, grid.z);
+            if (first)
+                k_cheb_poisson_pair<T, DIM, true><<<g2, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, (T)c1, (T)c2, ctl);
+            else
+                k_cheb_poisson_pair<T, DIM, false><<<g2, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, (T)c1, (T)c2, ctl);
+            return;
+        }
         if (first)
             k_cheb_stencil<T, DIM, true, true, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f, (T)c1,
                                                                            (T)c2, T(0), T(1), ctl);
@@ -542,6 +724,19 @@ cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, d
         const T ca = (T)(jacobi ? c * (1.0 - sigma) + c / D : c * (D + 1.0 - sigma));
         const T cb = (T)(jacobi ? -c / D : -c);
         const dim3 grid = box_grid(op), block(BX, BY);
+        if (std::is_same<T, float>::value) {
+            const float* pf = (const float*)p;
+            const float* qf = (const float*)q;
+            float* of = (float*)out;
+            if (op.dim == 3) {
+                if (first) k_cheb_box_f32<3, true><<<grid, block, 0, st>>>(pf, qf, of, op.nx, op.ny, op.nz, (float)ca, (float)cb, ctl);
+                else k_cheb_box_f32<3, false><<<grid, block, 0, st>>>(pf, qf, of, op.nx, op.ny, op.nz, (float)ca, (float)cb, ctl);
+            } else {
+                if (first) k_cheb_box_f32<2, true><<<grid, block, 0, st>>>(pf, qf, of, op.nx, op.ny, op.nz, (float)ca, (float)cb, ctl);
+                else k_cheb_box_f32<2, false><<<grid, block, 0, st>>>(pf, qf, of, op.nx, op.ny, op.nz, (float)ca, (float)cb, ctl);
+            }
+            return cudaGetLastError();
+        }
         if (op.dim == 3) {
             if (first) k_cheb_box<T, 3, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
             else k_cheb_box<T, 3, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
@@ -606,6 +801,13 @@ cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, 
         const Faces<double> f = faces_of<double>(op);
         const double d2 = 2.0 * op.dim;
         const bool poisson = op.wx == nullptr;
+        // (b, x, r must be 16-byte aligned for the pair kernel; the workspace columns are)
+        if (poisson && op.nx % 2 == 0 && aligned16(b) && aligned16(x) && (!r || aligned16(r)) && (!r32 || aligned8(r32))) {
+            const dim3 g2((op.nx + 2 * BX - 1) / (2 * BX), grid.y, grid.z);
+            if (op.dim == 3) k_residual_poisson_pair<3><<<g2, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, d2, partials, ctl, mode);
+            else k_residual_poisson_pair<2><<<g2, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, d2, partials, ctl, mode);
+            return cudaGetLastError();
+        }
         if (op.dim == 3) {
             if (poisson) k_residual_stencil<3, true><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
             else k_residual_stencil<3, false><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);

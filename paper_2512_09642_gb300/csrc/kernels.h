@@ -66,6 +66,11 @@ struct GramArgs {
     int64_t n, ld;
     const void* P;             // column-major n x (s+1), double or float
     bool fp32;
+    // block-conjugated form (FP64, s <= 16): C / d partials of launch_conj_cd and the state
+    // [W_(k-1) | B_k]; conj = 0 for the plain iteration
+    int conj, conj_nblk;
+    const double* conj_partials;
+    double* cj;
 };
 cudaError_t launch_gram(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st);
 int gram_blocks(const GramArgs& g, int sm_count);
@@ -86,6 +91,19 @@ cudaError_t launch_update(const UpdateArgs& u, const Ctl* ctl, cudaStream_t st);
 // Mixed form: x += P alpha / scale with FP32 P (compensated FP32 sum, exact FP64 add-in).
 cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
                                 cudaStream_t st);
+
+// Block-conjugated form (FP64, s <= 16). The workspace holds, at stride ld, the columns
+// P_+ = [p_0 .. p_s] (0 .. s), Q_(k-1) (s+1 .. 2s) and A Q_(k-1) (2s+1 .. 3s).
+// launch_conj_cd: per-block partials of C = (A Q_(k-1))^T P_k (s x s, row i = column i of
+// A Q) and d = Q_(k-1)^T r_k (s), S*S + S doubles per block, for the Gram kernel's last block.
+// launch_update_conj: Q_k = P_k - Q_(k-1) B, A Q_k = A P_k - A Q_(k-1) B (A P_k through the
+// Chebyshev change of basis), x += Q_k alpha, r = r_k - A Q_k alpha, all in place.
+cudaError_t launch_conj_cd(int s, const double* W, int64_t ld, int64_t n, double* partials, int nblk, const Ctl* ctl,
+                           cudaStream_t st);
+int conj_cd_blocks(int s, int64_t n, int sm_count);
+cudaError_t launch_update_conj(int s, double* W, int64_t ld, int64_t n, const double* diag, double dconst,
+                               double theta, double sigma, const double* cj, double* x, const Ctl* ctl,
+                               cudaStream_t st);
 
 // Sets the graph while-node condition to (ctl->done == RUNNING).
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, cudaStream_t st);

@@ -94,6 +94,16 @@ def test_invalid_grid_rejected_on_host(abi, grid):
     assert ei.value.status == 1
 
 
+def test_block_conjugate_options_checked_on_host(abi):
+    with pytest.raises(abi.SStepError) as ei:
+        abi.sstep_cg_create_stencil(2, 8, 8, 1, None, abi.sstep_cg_default_opts(block_conjugate=2), stream=0)
+    assert ei.value.status == 1
+    for bad in (dict(precision="mixed"), dict(s=17)):
+        with pytest.raises(abi.SStepError) as ei:
+            abi.sstep_cg_create_stencil(2, 8, 8, 1, None, abi.sstep_cg_default_opts(block_conjugate=1, **bad), stream=0)
+        assert ei.value.status == 7
+
+
 def test_box_stencil_invalid_options_rejected_on_host(abi):
     with pytest.raises(abi.SStepError) as ei:
         abi.sstep_cg_create_box_stencil(3, 8, 8, 8, abi.sstep_cg_default_opts(s=0), stream=0)

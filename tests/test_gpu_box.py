@@ -158,7 +158,7 @@ def test_box_solve_is_deterministic():
 
 
 def test_box_full_solve_outer_counts_match_stored_oracle_runs():
-    """64^3 and 128^3 27-point Poisson (s = 8, nu = 25, Lanczos-10 bounds) to 1e-8 against
+    """64^3, 128^3 and 230^3 27-point Poisson (s = 8, nu = 25, Lanczos-10 bounds) to 1e-8 against
     the oracle's converged runs (tests/golden/oracle_outer_counts_box.txt), within the same
     band as the 7-point runs: the literal restarted method's count is sensitive to rounding."""
     path = os.path.join(os.path.dirname(__file__), "golden", "oracle_outer_counts_box.txt")
@@ -167,7 +167,7 @@ def test_box_full_solve_outer_counts_match_stored_oracle_runs():
         if line.startswith("poisson27_"):
             tok = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
             stored[int(line.split()[0].split("_")[1])] = int(tok["outer"])
-    for side in (64, 128):
+    for side in (64, 128, 230):
         p = W.poisson27(side)
         for form in ("direct", "moments"):
             sv = _box(p, bounds_mode="lanczos10", s=8, nu=25, tol=1e-8, gram_form=form)

@@ -45,6 +45,9 @@ CASES = [
     ("diffusion2d_stencil", lambda: W.make("d2", (45, 33), kappa_sigma=1.0, config=13), "stencil"),
     ("diffusion3d_stencil", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), "stencil"),
     ("diffusion3d_csr", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), "csr"),
+    # even nx: the two-points-per-thread Poisson kernels (ragged in every direction)
+    ("poisson3d_even_ragged", lambda: W.make("p3e", (70, 13, 11), config=17), "stencil"),
+    ("poisson2d_even_ragged", lambda: W.make("p2e", (130, 33), config=18), "stencil"),
 ]
 
 
@@ -118,6 +121,7 @@ SOLVE_CASES = [
     ("poisson3d_32_stencil_s8", lambda: W.poisson3d(32), "stencil", 8, 25),
     ("diffusion3d_ragged_s12", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), "stencil", 12, 30),
     ("diffusion2d_csr_s8", lambda: W.make("d2", (45, 33), kappa_sigma=0.5, config=13), "csr", 8, 20),
+    ("poisson3d_even_ragged_s8", lambda: W.make("p3e", (70, 13, 11), config=17), "stencil", 8, 25),
 ]
 
 
