@@ -13,6 +13,7 @@ the CPU oracle (numpy/scipy, one thread) instead, on a bounded sample of outer i
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -142,6 +143,35 @@ def measured_peaks():
         d = json.load(open(path))
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def kernel_source_sha(path, kernel):
+    """sha256 of a kernel's __global__ definition (up to its closing brace at column 0)."""
+    import hashlib
+    src = open(os.path.join(ROOT, path)).read()
+    m = re.search(r"__global__ void __launch_bounds__\([^)]*\) " + re.escape(kernel) + r"\(", src)
+    if not m:
+        return None
+    end = src.find("\n}\n", m.start())
+    return hashlib.sha256(src[m.start():end + 3].encode()).hexdigest() if end >= 0 else None
+
+
+def measured_traffic(workload, form, logical):
+    """ncu DRAM bytes per launch for this bench line's dominant kernel, or None when no capture
+    exists or the kernel changed since it was taken."""
+    if not os.path.exists(TRAFFIC):
+        return None
+    for line in open(TRAFFIC):
+        tok = line.split()
+        if len(tok) < 7 or line.startswith("#"):
+            continue
+        if tok[0] == workload and tok[1] == form and tok[2] == logical:
+            return {"bytes": int(tok[5]), "kernel": tok[3], "profile": tok[7] if len(tok) > 7 else None} \
+                if kernel_source_sha(tok[4], tok[3]) == tok[6] else None
+    return None
 
 
 # FP64 pipe rate derived from the nominal 1.25 TFLOP/s FP64 of GB300 (152 SMs, 2070 MHz):
@@ -445,6 +475,11 @@ def run_ours(args):
                 forms[prec]["rel_diff_vs_fp64_x"] = float(torch.linalg.norm(res[prec]["x"] - x64) / torch.linalg.norm(x64))
     head = args.forms.split(",")[0]
     h = forms[head]
+    if h["roofline"]:
+        tr = measured_traffic(wname, head, h["roofline"].get("kernel"))
+        if tr:
+            h["roofline"]["traffic"] = tr["bytes"]
+            h["roofline"]["traffic_source"] = f"ncu capture of {tr['kernel']}, profiles/{tr['profile']}"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("poisson3d", "poisson27"):

