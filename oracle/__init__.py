@@ -13,7 +13,7 @@ product. Pinned by tests/test_oracle_pins.py against closed forms, textbook spec
 the paper's propositions. The claim kappa(G) = O(s^2) (Theorem "Polynomial Growth") is parity
 unpinned: it is recorded, not asserted.
 """
-from . import sstep_cg, spectral, adjoint, conjugated  # noqa: F401
+from . import sstep_cg, spectral, adjoint, conjugated, coarse  # noqa: F401
 from .sstep_cg import (  # noqa: F401
     Operator, chebyshev_basis, monomial_basis, gram, column_scaling, fgs, fgs_iterates,
     cholesky, cholesky_solve, solve, SolveResult,

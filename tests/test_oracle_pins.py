@@ -514,6 +514,57 @@ def test_scaled_solve_with_many_columns_matches_dense_solve():
     assert np.allclose(O.scaled_solve(Wm, R, 1, "cholesky"), np.linalg.solve(Wm, R), rtol=1e-12, atol=1e-12)
 
 
+# --- AMG coarse-grid FGS (Section 6) ------------------------------------------------------
+
+@pytest.mark.parametrize("dims,block", [((8, 6, 4), (2, 2, 2)), ((12, 8), (4, 4)), ((9, 6, 6), (3, 3, 3))])
+def test_coarse_operator_of_box_aggregation_is_scaled_coarse_laplacian(dims, block):
+    """Piecewise-constant aggregation of the Dirichlet Laplacian into b x ... x b boxes: the
+    aggregate sums give A_c = b^(d-1) times the Laplacian of the coarse grid (diagonal 2d
+    b^(d-1) from 2d b^d minus the in-box couplings, -b^(d-1) per face crossing)."""
+    from oracle import coarse as OC
+    op = O.Operator(*W.csr(dims))
+    agg, nc, cdims = OC.box_aggregates(dims, block)
+    Ac = OC.coarse_operator(op, agg, nc)
+    b = block[0]
+    Lc = _dense(O.Operator(*W.csr(cdims[:len(dims)])))
+    assert np.array_equal(Ac, b ** (len(dims) - 1) * Lc)
+
+
+def test_coarse_condition_number_independent_of_fine_size():
+    """Proposition "AMG Convergence": at a fixed coarse level kappa(A_c) does not grow with n_f
+    (here exactly constant: A_c is a scaled coarse Laplacian)."""
+    from oracle import coarse as OC
+    kap = []
+    for N in (8, 16, 32):
+        op = O.Operator(*W.csr((N, N, N)))
+        agg, nc, _ = OC.box_aggregates((N, N, N), (N // 4,) * 3)
+        ev = np.linalg.eigvalsh(OC.coarse_operator(op, agg, nc))
+        kap.append(ev[-1] / ev[0])
+    assert np.allclose(kap, kap[0], rtol=1e-10)
+
+
+@pytest.mark.parametrize("dims,block,sigma", [((13, 11), (3, 3), 1.0), ((7, 6, 5), (2, 3, 2), 0.5), ((10, 10), (1, 1), 0.7)])
+def test_streaming_coarse_fgs_equals_fgs_on_formed_operator(dims, block, sigma):
+    """Section 6's streaming form (A_c never formed, rows of A_c y from the fine level) gives
+    the FGS iterates of the formed A_c; ragged aggregates at the grid edge included; with 1 x 1
+    aggregates A_c = A_f."""
+    from oracle import coarse as OC
+    p = W.make("c", dims, kappa_sigma=sigma, config=51)
+    op = O.Operator(*p.csr())
+    agg, nc, _ = OC.box_aggregates(dims, block)
+    Ac = OC.coarse_operator(op, agg, nc)
+    if block == (1, 1):
+        assert np.allclose(Ac, _dense(op), rtol=0, atol=1e-14)
+    g = rng.normal(52, nc)
+    y0 = rng.uniform(53, nc)
+    for nu in (1, 3, 8):
+        a = OC.coarse_fgs(Ac, g, nu, y0)
+        s = OC.coarse_fgs_streaming(op, agg, nc, g, nu, y0)
+        assert np.linalg.norm(a - s) <= 1e-13 * np.linalg.norm(a), nu
+    ref = np.linalg.solve(Ac, g)
+    assert np.linalg.norm(OC.coarse_fgs(Ac, g, 2000) - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
 # --- adjoint ----------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dims", [(6, 5), (4, 3, 3)])
