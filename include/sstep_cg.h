@@ -218,6 +218,28 @@ SSTEP_API sstep_status sstep_cg_lanczos(sstep_cg_t handle, int k, uint64_t seed,
 SSTEP_API sstep_status sstep_convert_check(const double* in_d, int k, float* out_d, double* back_d, int64_t n,
                                            void* stream);
 
+/* --- AMG coarse-grid FGS ----------------------------------------------------------------- */
+
+enum { SSTEP_COARSE_FORMED = 0, SSTEP_COARSE_STREAMING = 1 };
+
+/* FGS as the AMG coarse-grid solver (Section 6, "AMG Coarse-Grid Extension") on the handle's
+ * matrix-free stencil operator A_f (sstep_cg_create_stencil or sstep_cg_create_box_stencil;
+ * CSR handles give SSTEP_ERR_UNSUPPORTED). The prolongation P aggregates bx x by x bz boxes of
+ * the grid (the last box along an axis may be smaller): column i of P is the indicator of
+ * aggregate i, ids x fastest over the ceil(nx/bx) x ceil(ny/by) x ceil(nz/bz) coarse grid
+ * (bz must be 1 in 2D). Runs nu forward Gauss-Seidel sweeps on A_c y = g with A_c = P^T A_f P,
+ * rows in increasing order, D = diag(A_c), starting from y_d: y_i += (g_i - (A_c y)_i) /
+ * (A_c)_ii.
+ *   mode SSTEP_COARSE_FORMED: A_c is assembled as a dense n_c x n_c matrix (n_c <= 16384;
+ *     n_c^2 doubles allocated for the call) and swept;
+ *   mode SSTEP_COARSE_STREAMING: A_c is never formed (Section 6's streaming form): P y is kept
+ *     on the fine grid and row i of A_c y is the sum of A_f (P y) over aggregate i; memory
+ *     O(n_f + n_c).
+ * g_d (double[n_c]) and y_d (double[n_c], in: y^(0), out: y^(nu)) are device arrays; the
+ * handle's residual scratch is used. Synchronises the handle's stream. */
+SSTEP_API sstep_status sstep_coarse_fgs(sstep_cg_t handle, int bx, int by, int bz, const double* g_d, double* y_d,
+                                        int nu, int mode);
+
 /* --- batched form -------------------------------------------------------------------- */
 
 typedef struct sstep_cg_batch_s* sstep_cg_batch_t;

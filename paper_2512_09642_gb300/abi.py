@@ -89,6 +89,7 @@ _SIGS = {
     "sstep_cg_batch_solve": (_I, [_VP, _VP, _VP, _VP, C.POINTER(Info)]),
     "sstep_cg_batch_destroy": (_I, [_VP]),
     "sstep_cg_batch_last_error": (C.c_char_p, [_VP]),
+    "sstep_coarse_fgs": (_I, [_VP, _I, _I, _I, _VP, _VP, _I, _I]),
     "sstep_gram_fgs_noalloc": (_I, [_I64, _I, _I, _I, _VP, _I64, _VP, _D, _D, _D, _VP, _VP]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -167,6 +168,16 @@ def sstep_cg_create_box_stencil(dim: int, nx: int, ny: int, nz: int, opts: Opts,
                                          _stream(stream))
     _check(st, None)
     return h
+
+
+COARSE_MODE = {"formed": 0, "streaming": 1}
+
+
+def sstep_coarse_fgs(h, block, g, y, nu: int, mode: str = "streaming"):
+    """nu coarse-grid FGS sweeps on A_c y = g (y updated in place), A_c = P^T A P for box
+    aggregates of size `block` = (bx, by[, bz])."""
+    bx, by, bz = (tuple(int(v) for v in block) + (1, 1))[:3]
+    _check(lib.sstep_coarse_fgs(h, bx, by, bz, _ptr(g), _ptr(y), int(nu), COARSE_MODE[mode]), h)
 
 
 def sstep_cg_solve(h, b, x, allow=(5,)) -> Info:

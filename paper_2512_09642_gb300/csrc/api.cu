@@ -843,6 +843,41 @@ sstep_status sstep_cg_create_box_stencil(sstep_cg_t* out, int dim, int nx, int n
     return SSTEP_OK;
 }
 
+sstep_status sstep_coarse_fgs(sstep_cg_t h, int bx, int by, int bz, const double* g_d, double* y_d, int nu, int mode) {
+    if (!h) return SSTEP_ERR_INVALID_ARG;
+    if (h->op.kind != OP_STENCIL) {
+        set_err(h, "coarse FGS needs a stencil handle (box aggregation of its grid)");
+        return SSTEP_ERR_UNSUPPORTED;
+    }
+    if (bx < 1 || by < 1 || bz < 1 || (h->op.dim == 2 && bz != 1) || nu < 1 || !g_d || !y_d ||
+        (mode != SSTEP_COARSE_FORMED && mode != SSTEP_COARSE_STREAMING)) {
+        set_err(h, "coarse FGS: need aggregate sizes >= 1 (bz = 1 in 2D), nu >= 1, device g and y, a known mode");
+        return SSTEP_ERR_INVALID_ARG;
+    }
+    const int64_t nc = (int64_t)((h->op.nx + bx - 1) / bx) * ((h->op.ny + by - 1) / by) * ((h->op.nz + bz - 1) / bz);
+    if (mode == SSTEP_COARSE_FORMED && nc > coarse_formed_max_nc()) {
+        set_err(h, "coarse FGS: formed A_c limited to n_c <= %d (got %lld); use the streaming mode",
+                coarse_formed_max_nc(), (long long)nc);
+        return SSTEP_ERR_INVALID_ARG;
+    }
+    double* dc = nullptr;
+    double* Ac = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (mode == SSTEP_COARSE_STREAMING) e = cudaMalloc(&dc, sizeof(double) * nc);
+    else e = cudaMalloc(&Ac, sizeof(double) * nc * nc);
+    if (e == cudaSuccess)
+        e = launch_coarse_fgs(h->op, bx, by, bz, (int)nc, g_d, y_d, nu, mode == SSTEP_COARSE_STREAMING, h->rtrue, dc,
+                              Ac, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dc);
+    cudaFree(Ac);
+    if (e != cudaSuccess) {
+        set_err(h, "coarse FGS: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? SSTEP_ERR_OOM : SSTEP_ERR_CUDA;
+    }
+    return SSTEP_OK;
+}
+
 sstep_status sstep_cg_solve(sstep_cg_t h, const double* b_d, double* x_d, sstep_cg_info* info) {
     if (!h) return SSTEP_ERR_INVALID_ARG;
     if (!b_d || !x_d || !aligned16(b_d) || !aligned16(x_d)) {

@@ -105,6 +105,14 @@ cudaError_t launch_update_conj(int s, double* W, int64_t ld, int64_t n, const do
                                double theta, double sigma, const double* cj, double* x, const Ctl* ctl,
                                cudaStream_t st);
 
+// FGS as the AMG coarse-grid solver (Section 6) on a stencil operator with bx x by x bz box
+// aggregation: nu sweeps on A_c y = g (y in place). streaming = 0: A_c formed into Ac
+// (nc * nc doubles, nc <= coarse_formed_max_nc()); 1: z (n doubles) and dc (nc doubles) as
+// scratch, A_c never formed.
+int coarse_formed_max_nc();
+cudaError_t launch_coarse_fgs(const OpDesc& op, int bx, int by, int bz, int nc, const double* g, double* y, int nu,
+                              int streaming, double* z, double* dc, double* Ac, cudaStream_t st);
+
 // Sets the graph while-node condition to (ctl->done == RUNNING).
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, cudaStream_t st);
 
