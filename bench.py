@@ -652,8 +652,8 @@ def run_coarse(args):
             "config": {"workload": "coarse_fgs_diffusion3d_128^3_agg8^3", "n_fine": p.n, "n_coarse": nc,
                        "nu": nu, "headline_mode": "streaming"},
             "modes": res,
-            "note": "Gauss-Seidel is sequential over the coarse rows: one warp (streaming) or one block "
-                    "(formed) walks them; the work per row is parallel"}))
+            "note": "Gauss-Seidel is sequential over the coarse rows: one block walks them; the work "
+                    "within a row is parallel"}))
 
 
 def main():

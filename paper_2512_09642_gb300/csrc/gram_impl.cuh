@@ -47,7 +47,7 @@ struct GramShape {
     static constexpr int M = (MOM ? 2 * S : NSYM + NLAST) + (DV ? S : 0);
     static constexpr int G = gram_roles(M, 46);     // warp roles, FP64 form
     static constexpr int NSLAB = GRAM_WARPS / G;
-    static constexpr int G32 = gram_roles(M, 28);   // warp roles, mixed form
+    static constexpr int G32 = gram_roles(M, 16);   // warp roles, mixed form (two blocks per SM)
     static constexpr int NSLAB32 = GRAM_WARPS / G32;
 };
 
@@ -160,24 +160,11 @@ __device__ __forceinline__ void gram_role_f32(const float* __restrict__ P, int64
     float ah[MQ > 0 ? MQ : 1], al[MQ > 0 ? MQ : 1];
 #pragma unroll
     for (int k = 0; k < MQ; ++k) ah[k] = al[k] = 0.f;
-    // the next element's values are loaded while the current one is accumulated, so the
-    // loads overlap the FP32 work (without it every element waits a full memory latency)
-    float nv[S + 1], ndv = 0.f;
-    if (e0 < n) {
-#pragma unroll
-        for (int c = 0; c <= S; ++c) nv[c] = __ldg(P + c * ld + e0);
-        if constexpr (DV) ndv = __ldg(diag + e0);
-    }
     for (int64_t e = e0; e < n; e += stride) {
         float pv[S + 1];
 #pragma unroll
-        for (int c = 0; c <= S; ++c) pv[c] = nv[c];
-        const float dv = ndv;
-        if (e + stride < n) {
-#pragma unroll
-            for (int c = 0; c <= S; ++c) nv[c] = __ldg(P + c * ld + e + stride);
-            if constexpr (DV) ndv = __ldg(diag + e + stride);
-        }
+        for (int c = 0; c <= S; ++c) pv[c] = __ldg(P + c * ld + e);
+        const float dv = DV ? __ldg(diag + e) : 1.f;
         float dq[S];
         if constexpr (DV) {
 #pragma unroll
@@ -553,8 +540,10 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     }
 }
 
+// One block per SM for the FP64 forms (FP64-pipe bound); the FP32 (mixed) form is latency
+// bound and runs two blocks per SM (registers capped at 64).
 template <int S, bool DV, typename T, bool MOM>
-__global__ void __launch_bounds__(GRAM_THREADS, 1) k_gram(const T* __restrict__ P, int64_t ld,
+__global__ void __launch_bounds__(GRAM_THREADS, std::is_same<T, float>::value ? 2 : 1) k_gram(const T* __restrict__ P, int64_t ld,
                                                          const T* __restrict__ diag, int64_t n,
                                                          double* partials, Ctl* ctl, GramParams gp) {
     if (ctl->done) return;

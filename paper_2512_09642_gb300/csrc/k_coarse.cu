@@ -6,7 +6,7 @@
 //              block sweeps its rows, y held in shared memory;
 //   streaming  A_c is never formed: z = P y is kept on the fine grid, (A_c y)_i is the sum
 //              of (A_f z) over aggregate i, and y_i += delta adds delta to z on the aggregate
-//              (one warp walks the aggregates in order).
+//              (one block walks the aggregates in order).
 // Gauss-Seidel is sequential over the coarse rows; the parallelism is within a row (the dense
 // row's dot product, or the aggregate's points).
 #include "kernels.h"
@@ -106,30 +106,39 @@ __global__ void k_coarse_diag(OpDesc op, Agg g, int nc, double* __restrict__ dc)
     }
 }
 
-// Streaming sweeps: one warp, aggregates in increasing order.
-__global__ void __launch_bounds__(32) k_coarse_stream(OpDesc op, Agg g, int nc, int nu, const double* __restrict__ gv,
+constexpr int CS = 256;   // threads of the streaming block
+
+// Streaming sweeps: one block walks the aggregates in increasing order; its threads share an
+// aggregate's points. The block barrier after the z update orders it before the next row.
+__global__ void __launch_bounds__(CS) k_coarse_stream(OpDesc op, Agg g, int nc, int nu, const double* __restrict__ gv,
                                                       const double* __restrict__ dc, double* __restrict__ y,
-                                                      double* __restrict__ z) {
-    const int lane = threadIdx.x;
+                                                      double* z) {
+    __shared__ double red[CS / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int cap = agg_size(g);
     for (int sweep = 0; sweep < nu; ++sweep) {
         for (int a = 0; a < nc; ++a) {
             double s = 0.0;
-            for (int p = lane; p < cap; p += 32) {
+            for (int p = t; p < cap; p += CS) {
                 int i, j, k;
                 if (!agg_point(g, a, p, i, j, k)) break;
                 stencil_row(op, i, j, k, [&](int64_t col, double v) { s = fma(v, z[col], s); });
             }
             s = warp_sum(s);
+            if (lane == 0) red[warp] = s;
+            __syncthreads();
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < CS / 32; ++w) tot += red[w];
             const double d = dc[a];
-            const double delta = d != 0.0 ? (gv[a] - s) / d : 0.0;
-            if (lane == 0) y[a] += delta;
-            for (int p = lane; p < cap; p += 32) {
+            const double delta = d != 0.0 ? (gv[a] - tot) / d : 0.0;
+            if (t == 0) y[a] += delta;
+            for (int p = t; p < cap; p += CS) {
                 int i, j, k;
                 if (!agg_point(g, a, p, i, j, k)) break;
                 z[i + (int64_t)op.nx * j + (int64_t)op.nx * op.ny * k] += delta;
             }
-            __syncwarp();   // z updates visible to the whole warp before the next aggregate
+            __syncthreads();   // z updates (and the reads of red) complete before the next row
         }
     }
 }
@@ -151,31 +160,51 @@ __global__ void k_coarse_form(OpDesc op, Agg g, int nc, double* __restrict__ Ac)
 
 constexpr int CF = 1024;   // threads of the formed-sweep block
 
-// Formed sweeps: one block, y in shared memory; row a's dot product over all threads.
+// Formed sweeps: one block, y in shared memory; row a's dot product over all threads. The
+// next row of A_c (which does not depend on the update) is loaded while this row is reduced.
+constexpr int CPT = 16;   // row entries per thread held in registers (n_c <= CF * CPT)
+
 __global__ void __launch_bounds__(CF) k_coarse_fgs_formed(const double* __restrict__ Ac, int nc, int nu,
                                                           const double* __restrict__ gv, double* __restrict__ y) {
     extern __shared__ double ys[];
     __shared__ double red[CF / 32];
-    __shared__ double dlt;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int c = t; c < nc; c += CF) ys[c] = y[c];
     __syncthreads();
+    double cur[CPT], nxt[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int c = t + q * CF;
+        cur[q] = c < nc ? Ac[c] : 0.0;
+    }
     for (int sweep = 0; sweep < nu; ++sweep) {
         for (int a = 0; a < nc; ++a) {
-            const double* row = Ac + (size_t)a * nc;
+            // the row after a (wrapping to row 0 for the next sweep)
+            const double* nrow = Ac + (size_t)(a + 1 < nc ? a + 1 : 0) * nc;
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int c = t + q * CF;
+                nxt[q] = c < nc ? nrow[c] : 0.0;
+            }
             double s = 0.0;
-            for (int c = t; c < nc; c += CF) s = fma(row[c], ys[c], s);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int c = t + q * CF;
+                if (c < nc) s = fma(cur[q], ys[c], s);
+            }
             s = warp_sum(s);
             if (lane == 0) red[warp] = s;
             __syncthreads();
             if (t == 0) {
                 double tot = 0.0;
                 for (int w = 0; w < CF / 32; ++w) tot += red[w];
-                const double d = row[a];
+                const double d = Ac[(size_t)a * nc + a];
                 const double delta = d != 0.0 ? (gv[a] - tot) / d : 0.0;
                 ys[a] += delta;
             }
             __syncthreads();
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) cur[q] = nxt[q];
         }
     }
     for (int c = t; c < nc; c += CF) y[c] = ys[c];
@@ -188,7 +217,7 @@ int grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-int coarse_formed_max_nc() { return 16384; }
+int coarse_formed_max_nc() { return CF * CPT; }
 
 cudaError_t launch_coarse_fgs(const OpDesc& op, int bx, int by, int bz, int nc, const double* g, double* y, int nu,
                               int streaming, double* z, double* dc, double* Ac, cudaStream_t st) {
@@ -205,7 +234,7 @@ cudaError_t launch_coarse_fgs(const OpDesc& op, int bx, int by, int bz, int nc, 
     if (streaming) {
         k_coarse_prolong<<<grid_for(op.n, 256), 256, 0, st>>>(op, a, y, z);
         k_coarse_diag<<<grid_for(nc, 128), 128, 0, st>>>(op, a, nc, dc);
-        k_coarse_stream<<<1, 32, 0, st>>>(op, a, nc, nu, g, dc, y, z);
+        k_coarse_stream<<<1, CS, 0, st>>>(op, a, nc, nu, g, dc, y, z);
         return cudaGetLastError();
     }
     cudaError_t e = cudaMemsetAsync(Ac, 0, sizeof(double) * (size_t)nc * nc, st);
