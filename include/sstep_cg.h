@@ -50,7 +50,7 @@ typedef enum {
     SSTEP_ERR_NUMERICAL = 4,       /* NaN/Inf in the Gram system, or every column dropped */
     SSTEP_ERR_NO_CONVERGENCE = 5,  /* max_outer reached, or the true residual stayed above tol */
     SSTEP_ERR_TIMEOUT = 6,         /* a bounded device-side wait expired */
-    SSTEP_ERR_UNSUPPORTED = 7      /* valid request this build does not implement */
+    SSTEP_ERR_UNSUPPORTED = 7      /* valid request the library does not implement */
 } sstep_status;
 
 enum { SSTEP_BOUNDS_GIVEN = 0, SSTEP_BOUNDS_GERSH_LANCZOS10 = 1, SSTEP_BOUNDS_LANCZOS10 = 2 };

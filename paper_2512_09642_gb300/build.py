@@ -1,8 +1,11 @@
 """Builds the in-tree CUDA library libsstep_cg.so for GB300 (sm_103a).
 
 Each translation unit under csrc/ is compiled by nvcc in parallel into _build/, then linked
-into paper_2512_09642_gb300/libsstep_cg.so. Objects are reused when newer than their sources
-and the headers. Run `python -m paper_2512_09642_gb300.build` or call build().
+into paper_2512_09642_gb300/libsstep_cg.so. The Gram instantiation units (INSTANCED) are
+compiled once per basis size s with -DSSTEP_INST_S=<s>: their cost grows steeply with s, so
+one object per s, started largest first, keeps the longest compile near a minute. Objects are
+reused when newer than their sources and the headers. Run
+`python -m paper_2512_09642_gb300.build` or call build().
 """
 from __future__ import annotations
 
@@ -30,13 +33,30 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libsstep_cg.so")
 
 
+# translation units compiled once per basis size s, and the sizes
+INSTANCED = {"k_gram_inst.cu": range(1, 33), "k_batch_gram_inst.cu": range(1, 17)}
+
+
+def _units():
+    """(source, object, extra flags, relative cost) for every compile job."""
+    units = []
+    for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
+        base = os.path.basename(src)[:-3]
+        if os.path.basename(src) in INSTANCED:
+            for s in INSTANCED[os.path.basename(src)]:
+                units.append((src, os.path.join(BUILD, f"{base}_s{s:02d}.o"), [f"-DSSTEP_INST_S={s}"], s * s))
+        else:
+            units.append((src, os.path.join(BUILD, base + ".o"), [], 0))
+    return units
+
+
 def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
-def _compile(nvcc, src, obj, verbose):
-    cmd = [nvcc] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
+def _compile(nvcc, src, obj, extra, verbose):
+    cmd = [nvcc] + ARCH + FLAGS + extra + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr[-4000:]}")
@@ -47,23 +67,22 @@ def build(verbose: bool = False, jobs: int = 0) -> str:
     """Compiles (if needed) and links the library; returns its path."""
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = max(os.path.getmtime(h) for h in _headers())
     todo, objs = [], []
-    for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+    for s, o, extra, cost in _units():
         objs.append(o)
         if not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr_time):
-            todo.append((s, o))
+            todo.append((cost, s, o, extra))
+    todo.sort(key=lambda u: -u[0])   # the longest compiles first
     jobs = jobs or min(len(todo) or 1, os.cpu_count() or 4)
     logs = []
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        futs = {ex.submit(_compile, nvcc, s, o, verbose): s for s, o in todo}
+        futs = {ex.submit(_compile, nvcc, s, o, extra, verbose): os.path.basename(o) for _, s, o, extra in todo}
         for f in cf.as_completed(futs):
             logs.append((futs[f], f.result()))
     if verbose:
         for s, log in sorted(logs):
-            sys.stderr.write(f"== {os.path.basename(s)}\n{log}")
+            sys.stderr.write(f"== {s}\n{log}")
     if todo or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + ".tmp"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]

@@ -1,4 +1,4 @@
-// Dispatch of the batched Gram + FGS kernel over s (instantiated in k_batch_gram_a/b.cu).
+// Dispatch of the batched Gram + FGS kernel over s (instantiated by k_batch_gram_inst.cu, once per s).
 #include "batch_impl.cuh"
 
 namespace sstep {

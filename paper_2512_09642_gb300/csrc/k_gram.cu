@@ -1,5 +1,5 @@
-// Dispatch of the fused Gram + FGS kernel over the basis size s (instantiated in
-// k_gram_s1.cu .. k_gram_s8.cu, four values of s each, so they compile in parallel).
+// Dispatch of the fused Gram + FGS kernel over the basis size s (instantiated by
+// k_gram_inst.cu, compiled once per s so the instantiations build in parallel).
 #include "gram_impl.cuh"
 
 namespace sstep {
