@@ -45,12 +45,15 @@ def parse():
                          "Chebyshev moments; +conj: block-conjugated s-step CG); the first is the headline")
     ap.add_argument("--graph", action="store_true", help="run the outer loop as one CUDA graph (no kernel sampling)")
     ap.add_argument("--workload", default="poisson3d",
-                    choices=["poisson3d", "poisson27", "poisson2d_64", "diffusion3d", "batch", "coarse"],
+                    choices=["poisson3d", "poisson27", "poisson2d_64", "diffusion3d", "batch", "coarse", "sweep"],
                     help="poisson3d: the headline 3D Poisson solve (--side); poisson27: 3D 27-point Poisson "
                          "--side (230, 12.2M unknowns), Lanczos-10 bounds; poisson2d_64: 2D Poisson 64^2 CSR, "
                          "s = 4, nu = 20; diffusion3d: 3D diffusion --side (384), log-normal kappa, s = 12, "
                          "nu = 30; batch: 512 uneven 2D diffusion systems; coarse: AMG coarse-grid FGS, "
-                         "3D diffusion 128^3 aggregated into 8^3 boxes (n_c = 4096), nu = 20")
+                         "3D diffusion 128^3 aggregated into 8^3 boxes (n_c = 4096), nu = 20; sweep: 3D Poisson "
+                         "--side (512, 134M unknowns), s in 4, 8, 12, 16, --sweep-outers outer iterations per "
+                         "solve, per-kernel bandwidth and FP64 rate")
+    ap.add_argument("--sweep-outers", type=int, default=16)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain-loop", action="store_true")
@@ -314,8 +317,10 @@ def run_reference(args):
     }))
 
 
-def measure_form(args, p, b, world, local, precision, csr=None):
-    """Warm-up + K timed solves of one form; per-kernel durations from the sampled events."""
+def measure_form(args, p, b, world, local, precision, csr=None, fixed_outers=None):
+    """Warm-up + K timed solves of one form; per-kernel durations from the sampled events.
+    fixed_outers: run exactly that many outer iterations per solve (tol 1e-30), sampling the
+    kernels in every chunk of 8, and skip the end-to-end leg."""
     import torch
     from paper_2512_09642_gb300 import SStepCG, abi
 
@@ -325,6 +330,8 @@ def measure_form(args, p, b, world, local, precision, csr=None):
     kw = dict(s=s, nu=args.nu, tol=1e-8, check_every=8, profile_every=0 if args.graph else 4, precision=prec,
               gram_form="moments" if "mom" in parts else "direct", use_graph=1 if args.graph else 0,
               block_conjugate=1 if "conj" in parts else 0)
+    if fixed_outers:
+        kw.update(tol=1e-30, max_outer=int(fixed_outers), profile_every=1)
     if p.stencil == "box":
         kw["bounds_mode"] = "lanczos10"   # Section 8: Lanczos-10 estimates of both ends, 10% margins
     if csr is not None:
@@ -358,7 +365,7 @@ def measure_form(args, p, b, world, local, precision, csr=None):
     t_solve = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3, world)
 
     t_e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not fixed_outers:
         # end to end through the C ABI with pinned host buffers, copies inside the timed region
         bh = torch.as_tensor(p.b).pin_memory()
         xh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -658,10 +665,59 @@ def run_coarse(args):
                     "within a row is parallel"}))
 
 
+def run_sweep(args):
+    """Bandwidth sweep on 3D Poisson (7-point, 512^3 = 134M unknowns by default) over s in
+    {4, 8, 12, 16}, FP64 and mixed forms (moments Gram): each solve runs a fixed number of
+    outer iterations, and every kernel's CUDA-event time, sampled inside them, gives its
+    algorithmic GB/s and FP64 rate against the HBM and FP64-pipe roofs."""
+    import torch
+    from workloads import problems as W
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    side = args.side if args.side != 256 else 512
+    p = W.poisson3d(side)
+    n = p.n
+    b = torch.as_tensor(p.b).cuda()
+    rows = []
+    for s in (4, 8, 12, 16):
+        args.s = s
+        for prec in ("fp64+mom", "mixed+mom"):
+            r = measure_form(args, p, b, world, local, prec, fixed_outers=args.sweep_outers)
+            roof, table = kernel_report(args, n, r["infos"], prec)
+            outers = r["infos"][-1]["outer_iters"]
+            per_outer = r["t"] / outers
+            ob = outer_bytes(s, prec.startswith("mixed"), 3) * n
+            rows.append({"s": s, "form": prec, "outer_iters": outers, "ms_per_outer": per_outer * 1e3,
+                         "model_bytes_per_outer": ob, "hbm_gbs_model": ob / per_outer / 1e9,
+                         "dominant": {k: roof[k] for k in ("kernel", "bound", "frac", "alu_frac", "hbm_frac")},
+                         "kernels": {k: {f: v[f] for f in ("avg_launch_ms", "share", "hbm_gbs", "fp64_gops")}
+                                     for k, v in table.items() if v["avg_launch_ms"]},
+                         "clocks": r["clocks"],
+                         "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"]))})
+            torch.cuda.empty_cache()
+    if rank == 0:
+        head = next(rw for rw in rows if rw["s"] == 8 and rw["form"] == "fp64+mom")
+        hbm_peak, _ = measured_peaks()
+        print(json.dumps({
+            "metric": f"time per outer iteration, 3D Poisson {side}^3, s = 8 (sweep over s)",
+            "value": head["ms_per_outer"] / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_outer"] * head["outer_iters"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": f"synthetic (b = A x*, x* ~ U(-1,1) splitmix64 seed {1000 + p.meta['config']})",
+            "config": {"workload": f"poisson3d_7pt_{side}^3_s_sweep", "n": n, "nu": args.nu, "precond": "jacobi",
+                       "outer_iters_per_solve": args.sweep_outers, "l2": "inputs larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "peaks": {"hbm_gbs": hbm_peak, "fp64_gops": FP64_OPS_PEAK / 1e9},
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "sweep": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "coarse":
