@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "../../include/sstep_cg.h"
+#include "ieee_conv.cuh"
 
 namespace sstep {
 
@@ -51,39 +52,15 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Exact float -> double by rebuilding the IEEE-754 fields with integer instructions (FP32
-// exponent e + 896 = FP64 exponent, mantissa shifted left by 29). Keeps the conversion off
-// the FP64 pipe, which converts at the FP64 rate on this part. Zero keeps its sign;
-// subnormal, infinite and NaN inputs take the hardware conversion.
+// Exact float -> double and float(v * 2^k), rounded to nearest, built with integer
+// instructions from the IEEE-754 fields (ieee_conv.cuh): this part converts between FP32 and
+// FP64 at the FP64 rate, and no input class takes a hardware conversion.
 __device__ __forceinline__ double f2d_exact(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned ex = (u >> 23) & 0xffu;
-    if (ex == 0u) {
-        if ((u & 0x7fffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-        return (double)f;
-    }
-    if (ex == 0xffu) return (double)f;
-    const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u >> 3) & 0xfffffu);
-    return __hiloint2double((int)hi, (int)(u << 29));
+    return __longlong_as_double((long long)f32_to_f64_bits(__float_as_uint(f)));
 }
 
-// float(v * 2^k), rounded to nearest (ties to even), built from the IEEE-754 fields with
-// integer instructions: the FP64 exponent is rebiased by k - 896 and the 52-bit mantissa is
-// rounded to 23 bits (a round-up that overflows the mantissa carries into the exponent, which
-// is the correct result). Zero, subnormal, infinite and NaN inputs, and results outside the
-// normal FP32 range, take the FP64 path.
 __device__ __forceinline__ float d2f_scaled(double v, int k) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned hi = (unsigned)(b >> 32);
-    const int ex = (int)((hi >> 20) & 0x7ffu);
-    const int fe = ex - 1023 + 127 + k;
-    if (ex == 0 || ex == 0x7ff || fe <= 0 || fe >= 254) return __double2float_rn(ldexp(v, k));
-    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    const unsigned m = (unsigned)(mant >> 29);
-    const unsigned rest = (unsigned)(mant & 0x1FFFFFFFull);
-    unsigned bits = ((unsigned)fe << 23) | m;
-    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) bits += 1u;
-    return __uint_as_float((hi & 0x80000000u) | bits);
+    return __uint_as_float(f64_to_f32_scaled_bits((uint64_t)__double_as_longlong(v), k));
 }
 
 // Compensated FP32 arithmetic (Knuth's TwoSum, FMA-based TwoProduct; Ogita, Rump and
