@@ -358,18 +358,20 @@ sstep_status make_f32_operator(sstep_cg_t h) {
         nnz = last;
     }
     const bool faces = h->op.kind == OP_STENCIL && h->faces;
-    const int64_t total = nnz + (faces ? 3 * n : 0) + (h->diag ? n : 0) + (h->cdinv ? n : 0);
+    // every array starts on a 128-byte boundary (the FP32 Gram reads diag32 in 8-byte pairs)
+    auto pad = [](int64_t m) { return (m + 31) / 32 * 32; };
+    const int64_t total = pad(nnz) + (faces ? 3 * pad(n) : 0) + (h->diag ? pad(n) : 0) + (h->cdinv ? pad(n) : 0);
     if (total == 0) return SSTEP_OK;
     CK(cudaMalloc(&h->ops32, sizeof(float) * total));
     float* q = h->ops32;
-    if (nnz) { CK(launch_to_f32(h->op.vals, q, nnz, h->stream)); h->op.vals32 = q; q += nnz; }
+    if (nnz) { CK(launch_to_f32(h->op.vals, q, nnz, h->stream)); h->op.vals32 = q; q += pad(nnz); }
     if (faces) {
-        CK(launch_to_f32(h->faces, q, 3 * n, h->stream));
-        h->op.wx32 = q; h->op.wy32 = q + n; h->op.wz32 = q + 2 * n;
-        q += 3 * n;
+        for (int f = 0; f < 3; ++f) CK(launch_to_f32(h->faces + f * n, q + f * pad(n), n, h->stream));
+        h->op.wx32 = q; h->op.wy32 = q + pad(n); h->op.wz32 = q + 2 * pad(n);
+        q += 3 * pad(n);
     }
-    if (h->diag) { CK(launch_to_f32(h->diag, q, n, h->stream)); h->op.diag32 = q; q += n; }
-    if (h->cdinv) { CK(launch_to_f32(h->cdinv, q, n, h->stream)); h->op.cdinv32 = q; q += n; }
+    if (h->diag) { CK(launch_to_f32(h->diag, q, n, h->stream)); h->op.diag32 = q; q += pad(n); }
+    if (h->cdinv) { CK(launch_to_f32(h->cdinv, q, n, h->stream)); h->op.cdinv32 = q; q += pad(n); }
     return SSTEP_OK;
 }
 

@@ -160,11 +160,7 @@ __device__ __forceinline__ void gram_role_f32(const float* __restrict__ P, int64
     float ah[MQ > 0 ? MQ : 1], al[MQ > 0 ? MQ : 1];
 #pragma unroll
     for (int k = 0; k < MQ; ++k) ah[k] = al[k] = 0.f;
-    for (int64_t e = e0; e < n; e += stride) {
-        float pv[S + 1];
-#pragma unroll
-        for (int c = 0; c <= S; ++c) pv[c] = __ldg(P + c * ld + e);
-        const float dv = DV ? __ldg(diag + e) : 1.f;
+    auto element = [&](const float* pv, float dv) {
         float dq[S];
         if constexpr (DV) {
 #pragma unroll
@@ -175,6 +171,49 @@ __device__ __forceinline__ void gram_role_f32(const float* __restrict__ P, int64
         }
 #pragma unroll
         for (int k = 0; k < MQ; ++k) dot2_acc(RT.kind[k] == 0 ? dq[RT.a[k]] : pv[RT.a[k]], pv[RT.b[k]], ah[k], al[k]);
+    };
+    // moments form: two consecutive elements per thread and iteration, loaded as 8-byte pairs
+    // (ld is even and the columns 8-byte aligned): twice the loads in flight per warp, which
+    // this latency-bound pass needs (0.175 -> 0.143 ms at 256^3, s = 8); an odd last element
+    // is read alone. The direct form, with more accumulators per role, keeps one element per
+    // iteration, as does s = 4 with a vector M: two spilled registers there.
+    if constexpr (!MOM || (DV && S == 4)) {
+        for (int64_t e = e0; e < n; e += stride) {
+            float pv[S + 1];
+#pragma unroll
+            for (int c = 0; c <= S; ++c) pv[c] = __ldg(P + c * ld + e);
+            element(pv, DV ? __ldg(diag + e) : 1.f);
+        }
+    } else {
+        for (int64_t e = 2 * e0; e < n; e += 2 * stride) {
+            float pa[S + 1], pb[S + 1];
+            float da = 1.f, db = 1.f;
+            if (e + 1 < n) {
+#pragma unroll
+                for (int c = 0; c <= S; ++c) {
+                    const float2 v = __ldg(reinterpret_cast<const float2*>(P + c * ld + e));
+                    pa[c] = v.x;
+                    pb[c] = v.y;
+                }
+                if constexpr (DV) {
+                    if (((uintptr_t)diag & 7u) == 0u) {
+                        const float2 d2 = __ldg(reinterpret_cast<const float2*>(diag + e));
+                        da = d2.x;
+                        db = d2.y;
+                    } else {
+                        da = __ldg(diag + e);
+                        db = __ldg(diag + e + 1);
+                    }
+                }
+                element(pa, da);
+                element(pb, db);
+            } else {
+#pragma unroll
+                for (int c = 0; c <= S; ++c) pa[c] = __ldg(P + c * ld + e);
+                if constexpr (DV) da = __ldg(diag + e);
+                element(pa, da);
+            }
+        }
     }
     const int lane = threadIdx.x & 31;
 #pragma unroll
