@@ -1,0 +1,61 @@
+"""The algorithmic work model behind bench.py's roofline fractions, on the CPU: FP64 operations
+and HBM bytes per unknown of each kernel, counted from the arithmetic of each step (7-point
+Chebyshev step: 5 adds of the neighbour sum + 2 FMAs, reading p_j, p_(j-1) and writing
+p_(j+1); moments Gram: 2s FMAs over the s + 1 basis vectors; update: s FMAs for x and s + 1
+for r, reading the s + 1 vectors and x, writing x and r), and the rule that a stored ncu
+traffic figure is reported only while the kernel's source is unchanged."""
+import os
+import shutil
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_fp64_poisson_model_per_unknown():
+    for s in (4, 8, 12, 16):
+        m = bench.kernel_model(s, mom=True)
+        assert m["cheb_step"] == {"ops": 7, "bytes": 24}
+        assert m["gram_fgs"] == {"ops": 2 * s, "bytes": 8 * (s + 1)}
+        assert m["update"] == {"ops": 2 * s + 1, "bytes": 8 * (s + 1) + 24}
+        assert m["residual"] == {"ops": 8, "bytes": 24}
+        # direct Gram: the s(s+1)/2 symmetric entries and the s entries against p_s
+        assert bench.kernel_model(s)["gram_fgs"]["ops"] == s * (s + 1) // 2 + s
+    # 2D: 3 adds + 2 FMAs
+    assert bench.kernel_model(8, dim=2)["cheb_step"]["ops"] == 5
+    # 27-point box step: separable box sum (2 adds per axis) + 2 FMAs
+    assert bench.kernel_model(8, box=True)["cheb_step"] == {"ops": 8, "bytes": 24}
+
+
+def test_outer_iteration_bytes():
+    # FP64, s = 8: first step 16 B (no p_(j-1)), 7 more at 24 B, Gram 72 B, update 96 B
+    assert bench.outer_bytes(8) == 16 + 7 * 24 + 72 + 96 == 352
+    # mixed: FP32 steps (8 + 7 x 12 B), FP32 Gram 36 B, update 48 B, FP64 refresh 20 B
+    assert bench.outer_bytes(8, mixed=True) == 8 + 7 * 12 + 36 + 48 + 20
+    mixed = bench.kernel_model(8, mixed=True)
+    assert mixed["cheb_step"]["ops"] == 0 and mixed["gram_fgs"]["ops"] == 0
+
+
+def test_stored_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
+    row = None
+    for line in open(bench.TRAFFIC):
+        if not line.startswith("#") and len(line.split()) >= 7:
+            row = line.split()
+            break
+    assert row is not None
+    workload, form, logical, kernel, src, nbytes, sha = row[:7]
+    assert bench.kernel_source_sha(src, kernel) == sha      # the committed capture is current
+    got = bench.measured_traffic(workload, form, logical)
+    assert got is not None and got["bytes"] == int(nbytes) and got["kernel"] == kernel
+    # the same table against an edited kernel definition: no traffic figure
+    fake_root = tmp_path / "root"
+    shutil.copytree(os.path.join(ROOT, os.path.dirname(src)), fake_root / os.path.dirname(src))
+    path = fake_root / src
+    text = path.read_text()
+    i = text.index(kernel + "(")
+    j = text.index("{", i)
+    path.write_text(text[:j + 1] + "\n    // edited\n" + text[j + 1:])
+    monkeypatch.setattr(bench, "ROOT", str(fake_root))
+    assert bench.kernel_source_sha(src, kernel) not in (None, sha)
+    assert bench.measured_traffic(workload, form, logical) is None
