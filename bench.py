@@ -40,24 +40,30 @@ def parse():
     ap.add_argument("--nu", type=int, default=25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="fp64+mom,mixed+mom,fp64,mixed,fp64+mom+conj",
+    ap.add_argument("--forms", default=parse_default_forms(),
                     help="comma list of fp64, mixed, fp64+mom, mixed+mom, fp64+mom+conj (+mom: Gram from "
                          "Chebyshev moments; +conj: block-conjugated s-step CG); the first is the headline")
     ap.add_argument("--graph", action="store_true", help="run the outer loop as one CUDA graph (no kernel sampling)")
     ap.add_argument("--workload", default="poisson3d",
-                    choices=["poisson3d", "poisson27", "poisson2d_64", "diffusion3d", "batch", "coarse", "sweep"],
+                    choices=["poisson3d", "poisson27", "poisson2d_64", "diffusion3d", "batch", "coarse", "sweep",
+                             "spread"],
                     help="poisson3d: the headline 3D Poisson solve (--side); poisson27: 3D 27-point Poisson "
                          "--side (230, 12.2M unknowns), Lanczos-10 bounds; poisson2d_64: 2D Poisson 64^2 CSR, "
                          "s = 4, nu = 20; diffusion3d: 3D diffusion --side (384), log-normal kappa, s = 12, "
                          "nu = 30; batch: 512 uneven 2D diffusion systems; coarse: AMG coarse-grid FGS, "
                          "3D diffusion 128^3 aggregated into 8^3 boxes (n_c = 4096), nu = 20; sweep: 3D Poisson "
                          "--side (512, 134M unknowns), s in 4, 8, 12, 16, --sweep-outers outer iterations per "
-                         "solve, per-kernel bandwidth and FP64 rate")
+                         "solve, per-kernel bandwidth and FP64 rate; spread: outer-iteration counts and ms per "
+                         "outer iteration of 3D Poisson 128^3 and 256^3 for five seeded x* (1002 .. 1402), "
+                         "FP64 and mixed, direct and moments Gram")
     ap.add_argument("--sweep-outers", type=int, default=16)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain-loop", action="store_true")
     ap.add_argument("--cpu-outers", type=int, default=2)
+    ap.add_argument("--csr", action="store_true",
+                    help="poisson3d: give the operator as a CSR matrix (int32 indices, FP64 values) instead of the "
+                         "matrix-free stencil")
     return ap.parse_args()
 
 
@@ -186,13 +192,46 @@ def measured_traffic(workload, form, logical):
 FP64_OPS_PEAK = 0.625e12
 
 
-def kernel_model(s, mixed=False, dim=3, mom=False, diffusion=False, box=False, conj=False):
+def form_gram(form):
+    """Gram form of a bench form name: fp64 / mixed, +mom (moments), +fused (moments reduced
+    by the step kernels), +conj (block-conjugated), +rN (mixed: FP64 refresh every N outers)."""
+    parts = form.split("+")
+    return "fused" if "fused" in parts else ("moments" if "mom" in parts else "direct")
+
+
+def form_refresh(form):
+    for part in form.split("+"):
+        if re.fullmatch(r"r\d+", part):
+            return int(part[1:])
+    return 1
+
+
+def kernel_model(s, mixed=False, dim=3, mom=False, diffusion=False, box=False, conj=False, fused=False,
+                 write_r=False, csr=None):
     """Algorithmic FP64-pipe operations and HBM bytes per unknown per launch of the stencil
-    path (change-of-basis Gram; the derivation is in the design notes)."""
+    path (change-of-basis Gram; the derivation is in the design notes). fused: the step
+    kernels reduce the moments (2 FMAs per unknown and step in FP64) and the Gram launch only
+    sums per-block partials; write_r: the mixed update also writes the recursive FP32
+    residual (reads p_s, writes p_0)."""
     nbr = 2 * dim
     gram_fma = (2 * s if mom else s * (s + 1) // 2 + s) + (s if diffusion else 0)
     # box stencil: the 3^dim box sum by separable row / plane / z sums, 2 adds each
     box_sum = 2 * dim
+    if csr is not None:
+        # CSR with nnz/n = csr entries per row and the Jacobi diagonal as a vector M: the Gram
+        # and update are those of a vector M; the step reads the row's values (8 B, FP32 copy
+        # 4 B) and columns (4 B), its row pointer (4 B), p_j once (ideal caching of the
+        # gathers), p_(j-1), writes p_(j+1), and reads 2 theta / diag; nnz/n FMAs + 2 per row
+        m = kernel_model(s, mixed, dim, mom, True, False, conj, fused, write_r)
+        vb, wb = (4, 4) if mixed else (8, 8)
+        m["cheb_step"] = {"ops": 0 if mixed else csr + 2, "bytes": (vb + 4) * csr + 4 + 3 * wb + wb}
+        m["residual"] = {"ops": csr + 2, "bytes": 12 * csr + 4 + 16 + (4 if mixed else 8)}
+        return m
+    if fused:
+        m = kernel_model(s, mixed, dim, True, diffusion, box, conj, False, write_r)
+        m["cheb_step"] = dict(m["cheb_step"], ops=m["cheb_step"]["ops"] + (0 if mixed else 2))
+        m["gram_fgs"] = {"ops": 0, "bytes": 0}
+        return m
     if not mixed:
         return {
             # Poisson: 2 dim - 1 adds of the neighbour sum + 2 FMAs; box: the box sum + 2 FMAs;
@@ -219,20 +258,26 @@ def kernel_model(s, mixed=False, dim=3, mom=False, diffusion=False, box=False, c
         "cheb_step": {"ops": 0, "bytes": 12 + (4 * (dim + 1) if diffusion else 0)},
         # products and compensated sums on the FP32 pipe; reads s+1 FP32 vectors
         "gram_fgs": {"ops": 0, "bytes": 4 * (s + 1) + (4 if diffusion else 0)},
-        # one add + one FMA in FP64; reads s FP32 vectors and x, writes x
-        "update": {"ops": 2, "bytes": 4 * s + 16},
+        # one add + one FMA in FP64; reads s FP32 vectors and x, writes x (write_r: reads p_s
+        # and writes the FP32 residual too)
+        "update": {"ops": 2, "bytes": 4 * s + 16 + (8 if write_r else 0)},
         # FP64 residual and its norm (scaling and FP32 rounding use integer instructions);
         # reads x, b (+ faces), writes the FP32 p_0
         "residual": {"ops": (box_sum + 3) if box else nbr + 2, "bytes": 20 + (8 * (dim + 1) if diffusion else 0)},
     }
 
 
-def outer_bytes(s, mixed=False, dim=3, diffusion=False, conj=False):
-    m = kernel_model(s, mixed, dim, diffusion=diffusion, conj=conj)
-    first = 16 if not mixed else 8    # the first step reads no p_(j-1)
+def outer_bytes(s, mixed=False, dim=3, diffusion=False, conj=False, fused=False, refresh=1, csr=None):
+    """Algorithmic bytes per unknown of one outer iteration (mixed with refresh period N: the
+    FP64 refresh in one outer iteration of N, the recursive residual written in the others
+    but the last of each group)."""
+    m = kernel_model(s, mixed, dim, diffusion=diffusion, conj=conj, fused=fused, csr=csr)
+    # the first step reads no p_(j-1)
+    first = m["cheb_step"]["bytes"] - (4 if mixed else 8) if csr is not None else (16 if not mixed else 8)
     steps = m["cheb_step"]["bytes"] * (s - 1) + first
-    extra = m["residual"]["bytes"] if mixed else 0
-    return steps + m["gram_fgs"]["bytes"] + m["update"]["bytes"] + extra
+    extra = m["residual"]["bytes"] / refresh if mixed else 0
+    upd = m["update"]["bytes"] + (8 * (refresh - 1) / refresh if mixed else 0)
+    return steps + m["gram_fgs"]["bytes"] + upd + extra
 
 
 # ---- CPU oracle timing -----------------------------------------------------------------------
@@ -255,15 +300,73 @@ print(json.dumps(out))
 """
 
 
-def oracle_outer_times(side, s, nu, outers, reps, box=False):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def oracle_outer_times(side, s, nu, outers, reps, box=False, threads=1, maker=None):
+    """Seconds per solve of `outers` outer iterations of the oracle (numpy/scipy), `reps` times,
+    in a fresh process whose BLAS may use `threads` threads."""
+    t = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = CPU_SNIPPET.format(root=ROOT, side=side, s=s, nu=nu, reps=reps, outers=outers,
-                              maker="poisson27" if box else "poisson3d",
+                              maker=maker or ("poisson27" if box else "poisson3d"),
                               bounds="lanczos10" if box else "gersh_lanczos10")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+ORACLE_SOLUTION_SNIPPET = r"""
+import sys, time, json
+import numpy as np
+sys.path.insert(0, {root!r})
+import oracle as O
+from oracle import spectral as OS
+from workloads import problems as W
+p = W.diffusion3d({side}, s={s}, nu={nu})
+op = O.Operator(*p.csr())
+lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+t0 = time.perf_counter()
+res = O.solve(op, p.b, s={s}, nu={nu}, lam_min=lam[0], lam_max=lam[1], tol=1e-8)
+np.save({out!r}, res.x)
+print(json.dumps({{"seconds": time.perf_counter() - t0, "outer_iters": res.outer_iters,
+                  "rel_res_true": res.rel_res_true, "lam": [float(lam[0]), float(lam[1])]}}))
+"""
+
+
+def diffusion_error_vs_oracle(forms, side, s, nu):
+    """The CPU-baseline leg's check of the diffusion forms against the oracle: the oracle solves
+    the same log-normal diffusion problem at a size it finishes in under a minute (side^3) to
+    1e-8, and each GPU form solves it with the oracle's bounds; returns ||x - x_oracle|| /
+    ||x_oracle|| per form with both outer counts."""
+    import numpy as np
+    import torch
+    from paper_2512_09642_gb300 import SStepCG
+    from workloads import problems as W
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", ORACLE_SOLUTION_SNIPPET.format(root=ROOT, side=side, s=s, nu=nu, out=path)],
+                       capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    meta = json.loads(r.stdout.strip().splitlines()[-1])
+    xo = np.load(path)
+    os.unlink(path)
+    p = W.diffusion3d(side, s=s, nu=nu)
+    kappa = torch.as_tensor(p.kappa).cuda()
+    b = torch.as_tensor(p.b).cuda()
+    out = {"workload": f"diffusion3d_7pt_{side}^3_lognormal1", "oracle_outer_iters": meta["outer_iters"],
+           "oracle_rel_res_true": meta["rel_res_true"], "oracle_seconds_1_thread": meta["seconds"], "forms": {}}
+    for form in forms:
+        sv = SStepCG(grid=p.dims, kappa=kappa, bounds=tuple(meta["lam"]), s=s, nu=nu, tol=1e-8,
+                     precision=form.split("+")[0], gram_form=form_gram(form),
+                     refresh_period=form_refresh(form) if form.startswith("mixed") else 1)
+        x, info = sv.solve(b)
+        sv.close()
+        xg = x.cpu().numpy()
+        out["forms"][form] = {"rel_err_vs_oracle_x": float(np.linalg.norm(xg - xo) / np.linalg.norm(xo)),
+                              "outer_iters": info["outer_iters"], "rel_res_true": info["rel_res_true"],
+                              "status": info["status"]}
+    return out
 
 
 def stored_oracle_outers(side, box=False):
@@ -279,13 +382,36 @@ def stored_oracle_outers(side, box=False):
 
 
 def cpu_model():
+    """CPU model name (lscpu's "Model name", else /proc/cpuinfo's) and the host's core count."""
+    name = None
     try:
-        for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part")):
-                return line.split(":", 1)[1].strip()
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
         pass
-    return "unknown"
+    if not name:
+        fields = {}
+        try:
+            for line in open("/proc/cpuinfo"):
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
+        except OSError:
+            pass
+        name = fields.get("model name") or (f"implementer {fields.get('cpu implementer')} part {fields.get('cpu part')}"
+                                            if "cpu part" in fields else "unknown")
+    return f"{name}, {os.cpu_count()} cores"
+
+
+def poisson3d_config(side, s, nu, box=False):
+    """The workload description shared by both arms (the GPU line and the CPU oracle's)."""
+    return {"workload": f"poisson3d_27pt_{side}^3" if box else f"poisson3d_7pt_{side}^3", "n": side ** 3,
+            "operator": "3D 27-point Poisson" if box else "3D 7-point Poisson", "s": s, "nu": nu,
+            "precond": "jacobi", "bounds": "lanczos10 (both ends, 10% margins)" if box else "gershgorin + lanczos10",
+            "tol": 1e-8, "l2": "inputs larger than L2", "x0": "zero", "b": "A x*, x* ~ U(-1,1)"}
 
 
 # ---- arms ------------------------------------------------------------------------------------
@@ -295,23 +421,24 @@ def run_reference(args):
     if rank != 0:
         return
     outers_needed = stored_oracle_outers(args.side)
-    times = oracle_outer_times(args.side, args.s, args.nu, 1, args.warmup + args.steps)[args.warmup:]
-    per_outer = statistics.mean(times)
     if outers_needed is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle outer-iteration count for this size not stored "
                           "(run tests/golden/make_oracle_outer_counts.py)"}))
         return
+    cores = os.cpu_count() or 1
+    times = oracle_outer_times(args.side, args.s, args.nu, 1, args.warmup + args.steps, threads=cores)[args.warmup:]
+    per_outer = statistics.mean(times)
     value = per_outer * outers_needed
-    sample = (f"each step = 1 outer iteration of the {args.side}^3 solve on the oracle (numpy/scipy, 1 thread); "
-              f"time to 1e-8 = seconds per outer x {outers_needed} outer iterations the oracle needs "
-              f"(tests/golden/oracle_outer_counts.txt)")
+    sample = (f"each step = 1 outer iteration of the {args.side}^3 solve on the oracle (numpy/scipy; BLAS on "
+              f"{cores} threads, the rest single-threaded); time to 1e-8 = seconds per outer x {outers_needed} outer "
+              f"iterations the oracle needs (tests/golden/oracle_outer_counts.txt)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_outer * 1e3,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"poisson3d_7pt_{args.side}^3", "n": args.side ** 3, "s": args.s, "nu": args.nu,
-                   "precond": "jacobi", "tol": 1e-8},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (b = A x*, x* ~ U(-1,1) splitmix64 seed 1002)",
+        "config": poisson3d_config(args.side, args.s, args.nu),
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample,
                          "cpu": cpu_model()},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -328,8 +455,8 @@ def measure_form(args, p, b, world, local, precision, csr=None, fixed_outers=Non
     parts = precision.split("+")
     prec = parts[0]
     kw = dict(s=s, nu=args.nu, tol=1e-8, check_every=8, profile_every=0 if args.graph else 4, precision=prec,
-              gram_form="moments" if "mom" in parts else "direct", use_graph=1 if args.graph else 0,
-              block_conjugate=1 if "conj" in parts else 0)
+              gram_form=form_gram(precision), use_graph=1 if args.graph else 0,
+              block_conjugate=1 if "conj" in parts else 0, refresh_period=form_refresh(precision))
     if fixed_outers:
         kw.update(tol=1e-30, max_outer=int(fixed_outers), profile_every=1)
     if p.stencil == "box":
@@ -381,7 +508,7 @@ def measure_form(args, p, b, world, local, precision, csr=None, fixed_outers=Non
     return {"t": t_solve, "e2e": t_e2e, "infos": infos, "clocks": clk, "x": x}
 
 
-def kernel_report(args, n, infos, precision, dim=3, diffusion=False, box=False):
+def kernel_report(args, n, infos, precision, dim=3, diffusion=False, box=False, csr=None):
     s = args.s
     names = ["cheb_step", "gram_fgs", "update", "residual"]
     info = infos[-1]
@@ -394,10 +521,15 @@ def kernel_report(args, n, infos, precision, dim=3, diffusion=False, box=False):
     mixed = precision.startswith("mixed")
     mom = "+mom" in precision
     conj = "+conj" in precision
+    fused = form_gram(precision) == "fused"
+    per = form_refresh(precision) if mixed else 1
     launches = {"cheb_step": s * outers, "gram_fgs": outers, "update": outers,
-                "residual": (outers + 1 if mixed else 0) + 2 + info["refreshes"]}
+                "residual": (-(-outers // per) + 1 if mixed else 0) + 2 + info["refreshes"]}
     share = {nm: (per_launch[nm] or 0.0) * launches[nm] for nm in names}
-    model = kernel_model(s, mixed, dim=dim, mom=mom, diffusion=diffusion, box=box, conj=conj)
+    # the sampled outer iteration (the chunk's first with a refresh period above 1) writes the
+    # recursive residual in its update
+    model = kernel_model(s, mixed, dim=dim, mom=mom, diffusion=diffusion, box=box, conj=conj, fused=fused,
+                         write_r=mixed and per > 1, csr=csr)
     hbm_peak, peak_kind = measured_peaks()
     table = {}
     for nm in names:
@@ -441,6 +573,8 @@ def run_ours(args):
     elif args.workload == "diffusion3d":
         side = args.side if args.side != 256 else 384
         args.s, args.nu = 12, 30
+        if args.forms == parse_default_forms():
+            args.forms = "fp64+mom,mixed+mom,mixed+mom+r4"   # a vector M: no fused moments
         p = W.diffusion3d(side)
         wname, opname = f"diffusion3d_7pt_{side}^3_lognormal1", "matrix-free stencil"
     elif args.workload == "poisson27":
@@ -451,6 +585,9 @@ def run_ours(args):
         side = args.side
         p = W.poisson3d(side, s=args.s, nu=args.nu)
         wname, opname = f"poisson3d_7pt_{side}^3", "matrix-free stencil"
+        if args.csr:
+            csr = tuple(torch.as_tensor(a).cuda() for a in p.csr())
+            wname, opname = f"poisson3d_7pt_{side}^3_csr", "CSR (int32 indices, FP64 values)"
     box = p.stencil == "box"
     s, nu = args.s, args.nu
     n = p.n
@@ -461,17 +598,22 @@ def run_ours(args):
         r = measure_form(args, p, b, world, local, prec, csr)
         dim = len(p.dims)
         diff = p.kappa is not None
-        # (the per-kernel model covers the stencil operators; CSR and graph runs report times only)
-        roof, table = (kernel_report(args, n, r["infos"], prec, dim, diff, box) if not args.graph and csr is None
+        # (graph runs report times only: no kernel sampling inside a graph)
+        nnz_row = None if csr is None else float(csr[0][-1].item()) / n
+        roof, table = (kernel_report(args, n, r["infos"], prec, dim, diff, box, nnz_row) if not args.graph
                        else ({}, {}))
         info = r["infos"][-1]
         outers = info["outer_iters"]
         cj = "+conj" in prec
-        bytes_solve = outer_bytes(s, prec.startswith("mixed"), dim, diff, cj) * n * outers
+        fz = form_gram(prec) == "fused"
+        rp = form_refresh(prec) if prec.startswith("mixed") else 1
+        ob = outer_bytes(s, prec.startswith("mixed"), dim, diff, cj, fz, rp, nnz_row)
+        bytes_solve = ob * n * outers
         forms[prec] = {"time_s": r["t"], "outer_iters": outers, "status": sorted({i["status"] for i in r["infos"]}),
                        "rel_res_true": info["rel_res_true"], "outer_per_s": outers / r["t"],
                        "hbm_gbs_model": bytes_solve / r["t"] / 1e9,
-                       "model_bytes_per_outer": outer_bytes(s, prec.startswith("mixed"), dim, diff, cj) * n,
+                       "model_bytes_per_outer": ob * n,
+                       "ms_per_outer": r["t"] / max(outers, 1) * 1e3,
                        "e2e_s": r["e2e"], "roofline": roof, "kernels": table, "clocks": r["clocks"],
                        "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"]))}
         res[prec] = r
@@ -502,27 +644,46 @@ def run_ours(args):
                if stored else "the measured GPU solve")
         try:
             per = statistics.mean(oracle_outer_times(side, s, nu, args.cpu_outers, 1, box)) / args.cpu_outers
+            cores = os.cpu_count() or 1
+            per_all = statistics.mean(oracle_outer_times(side, s, nu, args.cpu_outers, 1, box, threads=cores)) \
+                / args.cpu_outers
             cpu = {"value": per * outers, "unit": "s", "cores": 1, "kind": "oracle", "cpu": cpu_model(),
                    "sample": f"{args.cpu_outers} outer iterations of the same {side}^3 solve on the oracle "
                              f"(numpy/scipy FP64, 1 thread), seconds per outer x {outers} outer iterations "
-                             f"to 1e-8 from {src}", "s_per_outer": per, "outer_iters": outers}
+                             f"to 1e-8 from {src}", "s_per_outer": per, "outer_iters": outers,
+                   "all_cores": {"value": per_all * outers, "unit": "s", "cores": cores, "s_per_outer": per_all,
+                                 "sample": f"the same, BLAS on {cores} threads (the rest of the oracle is "
+                                           f"single-threaded numpy/scipy)"}}
+        except Exception as ex:  # the CPU leg must not hide the GPU result
+            cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "diffusion3d":
+        try:
+            outers = h["outer_iters"]
+            per = statistics.mean(oracle_outer_times(side, s, nu, 1, 1, maker="diffusion3d"))
+            cpu = {"value": per * outers, "unit": "s", "cores": 1, "kind": "oracle", "cpu": cpu_model(),
+                   "sample": f"1 outer iteration of the same {side}^3 diffusion solve on the oracle (numpy/scipy "
+                             f"FP64, 1 thread), seconds per outer x the {outers} outer iterations of the GPU's "
+                             f"{head} solve", "s_per_outer": per, "outer_iters": outers,
+                   "error_vs_oracle": diffusion_error_vs_oracle(list(forms), 48, s, nu)}
         except Exception as ex:  # the CPU leg must not hide the GPU result
             cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
 
     if rank == 0:
         metric = METRIC if args.workload == "poisson3d" else f"time-to-1e-8 residual, {wname}: s-step CG"
+        if args.workload in ("poisson3d", "poisson27") and csr is None:
+            cfg = poisson3d_config(side, s, nu, box)
+        else:
+            cfg = {"workload": wname, "n": n, "operator": opname, "s": s, "nu": nu, "precond": "jacobi",
+                   "bounds": "gershgorin + lanczos10", "tol": 1e-8,
+                   "l2": "inputs larger than L2" if n * 8 * (s + 1) > 129e6 else "inputs fit in L2"}
         line = {
             "metric": metric, "value": h["time_s"], "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["time_s"] * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if head.startswith("fp64") else "f32 basis + f64 Gram/x/residual",
             "data": f"synthetic (b = A x*, x* ~ U(-1,1) splitmix64 seed {1000 + p.meta['config']})",
-            "config": {"workload": wname, "n": n, "operator": opname,
-                       "s": s, "nu": nu, "precond": "jacobi",
-                       "bounds": "lanczos10 (both ends, 10% margins)" if box else "gershgorin + lanczos10",
-                       "tol": 1e-8, "form": head, "graph": bool(args.graph),
-                       "l2": "inputs larger than L2" if n * 8 * (s + 1) > 129e6 else "inputs fit in L2",
-                       "parallelism": f"replicas x{world}"},
+            "config": cfg,
+            "form": head, "graph": bool(args.graph), "parallelism": f"replicas x{world}",
             "outer_iters": h["outer_iters"], "rel_res_true": h["rel_res_true"], "outer_per_s": h["outer_per_s"],
             "hbm_gbs_model": h["hbm_gbs_model"], "roofline": h["roofline"],
             "e2e": {"value": h["e2e_s"], "unit": "s", "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
@@ -715,6 +876,82 @@ def run_sweep(args):
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "sweep": rows}))
 
 
+SPREAD_SEEDS = (1002, 1102, 1202, 1302, 1402)
+GOLDEN_SEEDS = os.path.join(ROOT, "tests", "golden", "oracle_outer_counts_seeds.txt")
+
+
+def run_spread(args):
+    """Outer-iteration counts to 1e-8 of the restarted iteration over five seeded exact
+    solutions x* (b = A x*), at 128^3 and 256^3, for each form: the count moves with rounding
+    over hundreds of outer iterations, the time per outer iteration does not. The oracle's own
+    counts at 128^3 for the same seeds are read from tests/golden/oracle_outer_counts_seeds.txt."""
+    import torch
+    from paper_2512_09642_gb300 import SStepCG, abi
+    from workloads import problems as W
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    forms = args.forms.split(",") if args.forms != parse_default_forms() else \
+        ["fp64+mom", "fp64", "mixed+mom", "mixed"]
+    stored = {}
+    if os.path.exists(GOLDEN_SEEDS):
+        for line in open(GOLDEN_SEEDS):
+            if line.startswith("poisson3d_"):
+                name = line.split()[0]
+                tok = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                stored[name] = int(tok["outer"])
+    rows = []
+    clk = None
+    for side in (128, 256):
+        probs = [W.poisson3d(side, xstar_seed=sd) for sd in SPREAD_SEEDS]
+        bs = [torch.as_tensor(p.b).cuda() for p in probs]
+        for form in forms:
+            parts = form.split("+")
+            sv = SStepCG(grid=probs[0].dims, s=8, nu=25, tol=1e-8, check_every=8, precision=parts[0],
+                         gram_form=form_gram(form), refresh_period=form_refresh(form) if parts[0] == "mixed" else 1)
+            x = torch.zeros(probs[0].n, dtype=torch.float64, device="cuda")
+            for _ in range(max(args.warmup, 1)):
+                x.zero_()
+                abi.sstep_cg_solve(sv.h, bs[0], x)
+            if side == 256 and form == forms[0]:
+                clocks = ClockSampler(local)
+                clocks.start()
+            per = []
+            for sd, b in zip(SPREAD_SEEDS, bs):
+                x.zero_()
+                torch.cuda.synchronize()
+                inf = abi.sstep_cg_solve(sv.h, b, x).as_dict()
+                per.append({"xstar_seed": sd, "outer_iters": inf["outer_iters"], "time_s": inf["ms"] / 1e3,
+                            "ms_per_outer": inf["ms"] / max(inf["outer_iters"], 1), "status": inf["status"],
+                            "rel_res_true": inf["rel_res_true"],
+                            "oracle_outer_iters": stored.get(f"poisson3d_{side}_xstar{sd}")})
+            if side == 256 and form == forms[0]:
+                clk = clocks.stop()
+            sv.close()
+            cnt = sorted(r["outer_iters"] for r in per)
+            mso = sorted(r["ms_per_outer"] for r in per)
+            rows.append({"side": side, "form": form, "outer_min": cnt[0], "outer_median": cnt[len(cnt) // 2],
+                         "outer_max": cnt[-1], "ms_per_outer_median": mso[len(mso) // 2],
+                         "ms_per_outer_min": mso[0], "ms_per_outer_max": mso[-1], "runs": per})
+            torch.cuda.empty_cache()
+    if rank == 0:
+        head = next(r for r in rows if r["side"] == 256 and r["form"] == forms[0])
+        print(json.dumps({
+            "metric": "median time per outer iteration over five x* seeds, 3D Poisson 256^3, s = 8, nu = 25",
+            "value": head["ms_per_outer_median"] / 1e3, "unit": "s", "n_gpus": world, "steps": len(SPREAD_SEEDS),
+            "warmup": max(args.warmup, 1), "ms_per_step": head["ms_per_outer_median"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (b = A x*, x* ~ U(-1,1) splitmix64 seeds 1002, 1102, 1202, 1302, 1402)",
+            "config": {"workload": "poisson3d_7pt_128^3_and_256^3_xstar_spread", "s": 8, "nu": 25,
+                       "precond": "jacobi", "bounds": "gershgorin + lanczos10", "tol": 1e-8,
+                       "l2": "inputs larger than L2 at 256^3"},
+            "clocks": clk, "spread": rows}))
+
+
+def parse_default_forms():
+    return "fp64+mom,mixed+mom,fp64,mixed,fp64+mom+conj"
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -725,6 +962,8 @@ def main():
         run_batch(args)
     elif args.workload == "coarse":
         run_coarse(args)
+    elif args.workload == "spread":
+        run_spread(args)
     else:
         run_ours(args)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1:

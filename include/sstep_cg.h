@@ -58,7 +58,19 @@ enum { SSTEP_GRAM_SOLVE_FGS = 0, SSTEP_GRAM_SOLVE_CHOLESKY = 1 };
 enum { SSTEP_PRECISION_FP64 = 0, SSTEP_PRECISION_MIXED = 1 };
 enum { SSTEP_PRECOND_NONE = 0, SSTEP_PRECOND_JACOBI = 1 };
 enum { SSTEP_START_R = 0 };
-enum { SSTEP_GRAM_FORM_DIRECT = 0, SSTEP_GRAM_FORM_MOMENTS = 1 };
+/* How G = P^T A P and c = P^T r_k are formed (the Gram system of Section 2). A P is never
+ * stored: with the recurrence of the Definition "Chebyshev Polynomial Basis", A P = M P_+ B
+ * (P_+ = [p_0 .. p_s], B the tridiagonal change of basis).
+ *  DIRECT: one pass over P_+ reduces the s(s+1)/2 + s inner products <p_a, p_b>_M.
+ *  MOMENTS: p_j = T_j(A^) p_0 with A^ = theta (M^-1 A - sigma) self-adjoint in <u, v>_M, so
+ *    <p_i, p_j>_M = (mu_(i+j) + mu_|i-j|) / 2 with the Chebyshev moments mu_k = <p_0, T_k(A^) p_0>_M
+ *    (the spectral expansion of Section 4); one pass over P_+ reduces the 2s moments.
+ *  FUSED: the same moments, with no pass over the basis: the step kernel that writes p_(j+1)
+ *    also reduces <p_j, p_j>_M and <p_j, p_(j+1)>_M (mu_2j = 2 <p_j, p_j>_M - mu_0, mu_(2j+1) =
+ *    2 <p_j, p_(j+1)>_M - mu_1), so each basis vector is read once per outer iteration. Needs a
+ *    stencil operator with a constant M (the Poisson or box stencil, or precond NONE; otherwise
+ *    SSTEP_ERR_UNSUPPORTED) and block_conjugate = 0. */
+enum { SSTEP_GRAM_FORM_DIRECT = 0, SSTEP_GRAM_FORM_MOMENTS = 1, SSTEP_GRAM_FORM_FUSED = 2 };
 
 #define SSTEP_MAX_S 32
 
@@ -74,8 +86,11 @@ typedef struct {
     int precision;         /* SSTEP_PRECISION_FP64 or _MIXED (FP32 basis, FP64 Gram/x/residual) */
     int precond;           /* SSTEP_PRECOND_JACOBI (M = diag A) or _NONE (M = I) */
     int basis_start;       /* SSTEP_START_R: p_0 = r_k as written in Section 2 */
-    int gram_form;         /* how G is formed: DIRECT inner products or Chebyshev MOMENTS */
-    int refresh_period;    /* MIXED: recompute r = b - A x every this many outers (>= 1) */
+    int gram_form;         /* how G is formed: SSTEP_GRAM_FORM_DIRECT, _MOMENTS or _FUSED */
+    int refresh_period;    /* MIXED: recompute r = b - A x in FP64 in the first outer iteration of
+                              every group of this many (>= 1, default 1); the others update the
+                              FP32 residual recursively (r -= A P alpha through the change of
+                              basis) and test convergence on it. FP64: unused */
     int max_refresh;       /* true-residual restarts after recursive convergence (default 3) */
     uint64_t seed;         /* splitmix64 stream of the Lanczos start vector (default 5000) */
     int use_graph;         /* 1: run the outer loop as a CUDA graph with a device-side while
@@ -290,11 +305,16 @@ SSTEP_API const char* sstep_cg_batch_last_error(sstep_cg_batch_t batch);
  * (double[n]) or NULL for M = mconst * I (mconst > 0); lambda_min < lambda_max, the bounds the
  * basis was built with; nu sweeps; gram_solver SSTEP_GRAM_SOLVE_FGS or _CHOLESKY.
  * Output out_d (device, double[3s + s*s + 1]): alpha = S a (s), d (s), c~ (s), G~ (s*s,
- * row-major), then the termination state (0 = solved, 3 = numerical breakdown).
+ * row-major), then the termination state (0 = solved, 3 = numerical breakdown: the other
+ * entries are then NaN).
  * Limit: 1 <= s <= 16 (SSTEP_ERR_INVALID_ARG beyond, with the reason in
  * sstep_cg_last_error(NULL)). Asynchronous on `stream`.
- * The first call on a device looks up the device address of the static scratch
- * (cudaGetSymbolAddress with that device current); make it before any stream capture.
+ * The device address of the static scratch is looked up (cudaGetSymbolAddress with the device
+ * current) on the first call on a device and on every call whose stream is not capturing, as
+ * a device reset (cudaDeviceReset) moves it; a call during stream capture reuses the address
+ * of the device's last call outside capture. So make a first call on each device before any
+ * stream capture, and again after a device reset (a first call during capture gives
+ * SSTEP_ERR_INVALID_ARG).
  * All calls on a device share the scratch and it keeps the last call's contents (each call
  * re-initialises what must start at zero): calls whose work can overlap on the GPU, such as
  * calls on two streams, race - serialise them. */

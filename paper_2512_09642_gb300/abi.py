@@ -21,7 +21,7 @@ BOUNDS = {"given": 0, "gersh_lanczos10": 1, "lanczos10": 2}
 GRAM_SOLVER = {"fgs": 0, "cholesky": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 PRECOND = {"none": 0, "jacobi": 1}
-GRAM_FORM = {"direct": 0, "moments": 1}
+GRAM_FORM = {"direct": 0, "moments": 1, "fused": 2}
 
 
 class Opts(C.Structure):

@@ -33,6 +33,10 @@ struct sstep_cg_s {
     double* rtrue = nullptr;    // true residual b - A x
     double* gram_partials = nullptr;
     int gram_nblk = 0;
+    bool fused = false;         // gram_form FUSED: moments reduced by the step kernels
+    void* mom_part = nullptr;   // their per-block partials, s steps x 16 bytes x mom_nblk
+    int mom_nblk = 0;
+    double* mom_part2 = nullptr;   // the finish kernel's per-block sums
     double* res_partials = nullptr;
     bool conj = false;          // block-conjugated form: P holds P_+, Q_(k-1), A Q_(k-1)
     double* conj_partials = nullptr;
@@ -110,13 +114,15 @@ sstep_status validate_opts(sstep_cg_t h, const sstep_cg_opts* o) {
         set_err(h, "block_conjugate needs FP64 and s <= 16");
         return SSTEP_ERR_UNSUPPORTED;
     }
-    if (o->precision == SSTEP_PRECISION_MIXED && o->refresh_period != 1) {
-        set_err(h, "mixed precision refreshes r = b - A x every outer iteration (refresh_period 1)");
-        return SSTEP_ERR_UNSUPPORTED;
-    }
-    if (o->gram_form != SSTEP_GRAM_FORM_DIRECT && o->gram_form != SSTEP_GRAM_FORM_MOMENTS) {
+    if (o->refresh_period > 1000000) { set_err(h, "refresh_period > 10^6"); return SSTEP_ERR_INVALID_ARG; }
+    if (o->gram_form != SSTEP_GRAM_FORM_DIRECT && o->gram_form != SSTEP_GRAM_FORM_MOMENTS &&
+        o->gram_form != SSTEP_GRAM_FORM_FUSED) {
         set_err(h, "unknown gram_form %d", o->gram_form);
         return SSTEP_ERR_INVALID_ARG;
+    }
+    if (o->gram_form == SSTEP_GRAM_FORM_FUSED && o->block_conjugate) {
+        set_err(h, "gram_form FUSED does not combine with block_conjugate");
+        return SSTEP_ERR_UNSUPPORTED;
     }
 
     if (o->check_every < 1) { set_err(h, "check_every < 1"); return SSTEP_ERR_INVALID_ARG; }
@@ -172,7 +178,8 @@ sstep_status host_dot(sstep_cg_t h, const double* a, const double* b, double* pa
 
 int setup_nblk(int64_t n) {
     const int64_t b = (n + 255) / 256;
-    return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
+    const int64_t cap = 8 * (int64_t)device_sm_count();
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 // k Lanczos steps on B = M^-1/2 A M^-1/2 (Section 8), start vector splitmix64(seed) U(-1,1).
@@ -321,7 +328,10 @@ GramArgs gram_args(sstep_cg_t h) {
     g.s = h->opts.s;
     g.nu = h->opts.nu;
     g.solver = h->opts.gram_solver;
-    g.form = h->opts.gram_form;
+    // the fused form's moments come from the step kernels; a Gram pass over a given basis
+    // (sstep_cg_gram_solve) forms the same moments itself
+    g.form = h->opts.gram_form == SSTEP_GRAM_FORM_FUSED ? SSTEP_GRAM_FORM_MOMENTS : h->opts.gram_form;
+    g.check = h->mixed ? 0 : 1;
     g.theta = h->theta;
     g.sigma = h->sigma;
     g.dvec = h->jacobi && h->diag != nullptr;
@@ -402,6 +412,18 @@ sstep_status finish_create(sstep_cg_t h) {
         if ((st = make_f32_operator(h)) != SSTEP_OK) return st;
     }
     CK(cudaMalloc(&h->rtrue, sizeof(double) * n));
+    if (h->fused) {
+        // the step kernels reduce the moments: a stencil operator with a constant M (Poisson
+        // star or box stencil, or no preconditioner)
+        if (h->op.kind != OP_STENCIL || (h->jacobi && h->diag)) {
+            set_err(h, "gram_form FUSED needs a stencil operator with a constant preconditioner (Poisson or "
+                       "box stencil, or precond NONE)");
+            return SSTEP_ERR_UNSUPPORTED;
+        }
+        h->mom_nblk = cheb_step_blocks(h->op);
+        CK(cudaMalloc(&h->mom_part, (size_t)16 * h->mom_nblk * h->opts.s));
+        CK(cudaMalloc(&h->mom_part2, sizeof(double) * MAX_FIN_BLOCKS * 2 * h->opts.s));
+    }
     GramArgs g = gram_args(h);
     h->gram_nblk = gram_blocks(g, h->sm_count);
     CK(cudaMalloc(&h->gram_partials, sizeof(double) * gram_partials_needed(g, h->gram_nblk)));
@@ -429,6 +451,7 @@ sstep_status begin_create(sstep_cg_t* out, const sstep_cg_opts* opts, void* stre
     h->jacobi = o.precond == SSTEP_PRECOND_JACOBI;
     h->mixed = o.precision == SSTEP_PRECISION_MIXED;
     h->conj = o.block_conjugate != 0;
+    h->fused = o.gram_form == SSTEP_GRAM_FORM_FUSED;
     return SSTEP_OK;
 }
 
@@ -450,38 +473,53 @@ sstep_status fail_create(sstep_cg_t h, sstep_status st) {
     return st;
 }
 
-// One outer iteration: s Chebyshev steps, the fused Gram + FGS, the update (FP64 form), or
-// the FP64 residual refresh, s FP32 Chebyshev steps, the mixed Gram + FGS and the x update
-// (mixed form). With `prof`, events ev[0..] bracket every kernel.
-sstep_status launch_outer(sstep_cg_t h, const double* b, double* x, int* launches, bool prof) {
+// Kernels of one outer iteration (refresh: the mixed form's FP64 residual refresh runs).
+int outer_kernels(sstep_cg_t h, bool refresh) {
+    return h->opts.s + 2 + (h->mixed && refresh ? 1 : 0) + (h->conj ? 1 : 0);
+}
+
+// One outer iteration: s Chebyshev steps, the Gram + FGS (or the fused form's finish), the
+// update (FP64 form); or, in the mixed form, the FP64 residual refresh when `refresh` is set
+// (else the FP32 p_0 the previous update wrote), s FP32 Chebyshev steps, the Gram + FGS and the
+// x update, which also writes the next FP32 p_0 when `write_r` is set (the next outer
+// iteration does not refresh). With `prof`, events ev[0..] bracket every kernel.
+sstep_status launch_outer(sstep_cg_t h, const double* b, double* x, int* launches, bool prof, bool refresh = true,
+                          bool write_r = false) {
     const int s = h->opts.s;
     int ev = 0;
     if (prof) CK(cudaEventRecord(h->ev[ev++], h->stream));
-    if (h->mixed) {
+    if (h->mixed && refresh) {
         CK(launch_residual(h->op, b, x, nullptr, h->P32, h->res_partials, h->ctl, 2, h->stream));
         if (prof) CK(cudaEventRecord(h->ev[ev++], h->stream));
     }
     for (int j = 0; j < s; ++j) {
+        void* mom = h->fused ? (void*)((char*)h->mom_part + (size_t)16 * h->mom_nblk * j) : nullptr;
         if (h->mixed) {
             const float* p = h->P32 + (int64_t)j * h->ld;
             const float* q = j > 0 ? h->P32 + (int64_t)(j - 1) * h->ld : nullptr;
             float* o = h->P32 + (int64_t)(j + 1) * h->ld;
-            CK(launch_cheb_step<float>(h->op, p, q, o, h->theta, h->sigma, j == 0, h->jacobi, h->ctl, h->stream));
+            CK(launch_cheb_step<float>(h->op, p, q, o, h->theta, h->sigma, j == 0, h->jacobi, h->ctl, h->stream, mom));
         } else {
             const double* p = h->P + (int64_t)j * h->ld;
             const double* q = j > 0 ? h->P + (int64_t)(j - 1) * h->ld : nullptr;
             double* o = h->P + (int64_t)(j + 1) * h->ld;
-            CK(launch_cheb_step<double>(h->op, p, q, o, h->theta, h->sigma, j == 0, h->jacobi, h->ctl, h->stream));
+            CK(launch_cheb_step<double>(h->op, p, q, o, h->theta, h->sigma, j == 0, h->jacobi, h->ctl, h->stream, mom));
         }
         if (prof) CK(cudaEventRecord(h->ev[ev++], h->stream));
     }
     GramArgs g = gram_args_outer(h);
+    if (h->mixed) g.check = refresh ? 0 : 2;
     if (h->conj)   // C and d for the block conjugation (timed with the Gram)
         CK(launch_conj_cd(s, h->P, h->ld, h->op.n, h->conj_partials, h->conj_nblk, h->ctl, h->stream));
-    CK(launch_gram(g, h->gram_partials, h->ctl, h->gram_nblk, h->stream));
+    if (h->fused) {
+        g.fp32 = h->mixed;
+        CK(launch_moments_finish(g, h->mom_part, h->mom_nblk, h->mom_part2, h->ctl, h->stream));
+    } else {
+        CK(launch_gram(g, h->gram_partials, h->ctl, h->gram_nblk, h->stream));
+    }
     if (prof) CK(cudaEventRecord(h->ev[ev++], h->stream));
     if (h->mixed) {
-        CK(launch_update_mixed(h->P32, h->ld, s, h->op.n, x, h->ctl, h->stream));
+        CK(launch_update_mixed(h->P32, h->ld, s, h->op.n, x, h->ctl, h->stream, write_r, g.dvec ? h->op.diag32 : nullptr));
     } else if (h->conj) {
         CK(launch_update_conj(s, h->P, h->ld, h->op.n, g.dvec ? h->diag : nullptr, g.dconst, h->theta, h->sigma,
                               h->cj, x, h->ctl, h->stream));
@@ -499,16 +537,20 @@ sstep_status launch_outer(sstep_cg_t h, const double* b, double* x, int* launche
         CK(launch_update(u, h->ctl, h->stream));
     }
     if (prof) CK(cudaEventRecord(h->ev[ev++], h->stream));
-    *launches += s + 2 + (h->mixed ? 1 : 0) + (h->conj ? 1 : 0);
+    *launches += outer_kernels(h, refresh);
     return SSTEP_OK;
 }
 
+// Outer iterations per group: the mixed form refreshes the FP64 residual in the first outer
+// iteration of each group of refresh_period; the FP64 form keeps its recursive residual.
+int group_size(sstep_cg_t h) { return h->mixed ? h->opts.refresh_period : 1; }
+
 // Adds the kernel times of the last profiled outer iteration (events complete) to inf.
-sstep_status collect_outer_profile(sstep_cg_t h, sstep_cg_info* inf) {
+sstep_status collect_outer_profile(sstep_cg_t h, sstep_cg_info* inf, bool refreshed) {
     const int s = h->opts.s;
     float ms = 0.f;
     int ev = 0;
-    if (h->mixed) {
+    if (h->mixed && refreshed) {
         CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
         inf->prof_ms[3] += ms;
         inf->prof_launches[3] += 1;
@@ -583,7 +625,9 @@ sstep_status build_graph(sstep_cg_t h, const double* b, double* x) {
     cudaStream_t user = h->stream;
     h->stream = h->cap_stream;
     int dummy = 0;
-    sstep_status st = launch_outer(h, b, x, &dummy, false);
+    sstep_status st = SSTEP_OK;
+    const int grp = group_size(h);
+    for (int m = 0; m < grp && st == SSTEP_OK; ++m) st = launch_outer(h, b, x, &dummy, false, m == 0, m + 1 < grp);
     cudaError_t e = st == SSTEP_OK ? launch_loop_cond(ch, h->ctl, h->cap_stream) : cudaSuccess;
     h->stream = user;
     cudaGraph_t captured = nullptr;
@@ -630,11 +674,16 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
     ++launches;
     sstep_status status = SSTEP_OK;
     int refreshes = 0;
-    const int outer_launches = h->opts.s + 2 + (h->mixed ? 1 : 0) + (h->conj ? 1 : 0);
+    const int grp = group_size(h);
+    // kernels of one pass of the graph body: a group of outer iterations and the condition
+    const int body_launches = outer_kernels(h, true) + (grp - 1) * outer_kernels(h, false) + 1;
     // conjugated form: the first block has no predecessor (Q_(-1) = A Q_(-1) = 0)
     if (h->conj)
         CK(cudaMemsetAsync(h->P + (int64_t)(h->opts.s + 1) * h->ld, 0, sizeof(double) * 2 * h->opts.s * h->ld,
                            h->stream));
+    // outer iterations launched in the current group sequence: the mixed form refreshes the FP64
+    // residual in outer iterations with in_group % refresh_period == 0, as the graph body does
+    long in_group = 0;
     for (long chunk = 0;; ++chunk) {
         if (h->opts.use_graph) {
             if (!h->gexec || h->g_b != b || h->g_x != x)
@@ -642,20 +691,27 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
             const int before = h->ctl_h->outer;
             CK(cudaGraphLaunch(h->gexec, h->stream));
             if ((st = read_ctl(h)) != SSTEP_OK) return st;
-            // kernels that ran: every body pass launches the outer's kernels and the condition
-            launches += (h->ctl_h->outer - before + 1) * (outer_launches + 1);
+            // kernels that ran: every body pass launches its group's kernels and the condition;
+            // the pass that saw the stop is the last
+            launches += ((h->ctl_h->outer - before) / grp + 1) * body_launches;
         } else {
             const bool prof = profiling && chunk % h->opts.profile_every == 0;
             // the sampled outer iteration is the chunk's second (the very first outer iteration
             // of a solve is not typical: in the conjugated form its previous block is zero)
-            const int sample = h->opts.check_every > 1 ? 1 : 0;
+            // (the mixed form with refresh_period > 1 samples the chunk's first outer iteration,
+            // which normally refreshes the FP64 residual)
+            const int sample = (h->mixed && grp > 1) || h->opts.check_every == 1 ? 0 : 1;
             const int before = h->ctl_h->outer;
-            for (int m = 0; m < h->opts.check_every; ++m)
-                if ((st = launch_outer(h, b, x, &launches, prof && m == sample)) != SSTEP_OK) return st;
+            const long m0 = in_group;
+            for (int m = 0; m < h->opts.check_every; ++m, ++in_group)
+                if ((st = launch_outer(h, b, x, &launches, prof && m == sample, in_group % grp == 0,
+                                       (in_group + 1) % grp != 0)) != SSTEP_OK)
+                    return st;
             if ((st = read_ctl(h)) != SSTEP_OK) return st;
             // keep the sample only if that outer iteration did its work (its kernels exit at once
             // after convergence)
-            if (prof && h->ctl_h->outer > before + sample && (st = collect_outer_profile(h, &inf)) != SSTEP_OK)
+            if (prof && h->ctl_h->outer > before + sample &&
+                (st = collect_outer_profile(h, &inf, (m0 + sample) % grp == 0)) != SSTEP_OK)
                 return st;
         }
         const int done = h->ctl_h->done;
@@ -668,6 +724,7 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
         const bool true_ok = c.r0_sq == 0.0 || c.true_sq < c.tol_sq * c.r0_sq;
         if (done == CONVERGED && !true_ok && refreshes < h->opts.max_refresh) {
             ++refreshes;
+            in_group = 0;   // the mixed form's next outer iteration loads the replaced residual
             CK(cudaMemcpyAsync(h->P, h->rtrue, sizeof(double) * h->op.n, cudaMemcpyDeviceToDevice, h->stream));
             const int zero = RUNNING;
             CK(cudaMemcpyAsync(&h->ctl->done, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -927,6 +984,8 @@ sstep_status sstep_cg_destroy(sstep_cg_t h) {
     cudaFree(h->ops32);
     cudaFree(h->rtrue);
     cudaFree(h->gram_partials);
+    cudaFree(h->mom_part);
+    cudaFree(h->mom_part2);
     cudaFree(h->res_partials);
     cudaFree(h->conj_partials);
     cudaFree(h->cj);

@@ -235,6 +235,7 @@ __device__ __forceinline__ void gram_role_dispatch32(int q, const float* P, int6
 struct GramParams {
     int nu, solver;
     int check;                   // 1: convergence / max-outer test on c_0 = ||r_k||^2 (FP64 form);
+                                 // 2: the same on c_0 / scale^2 (mixed form between refreshes);
                                  // 0: done by the FP64 residual refresh (mixed form)
     double theta, sigma, dfac;   // dfac: constant diagonal of M (1 when M = I); unused if DV
     // block-conjugated form (conj = 1): per-block partials of C = (A Q_(k-1))^T P_k and
@@ -440,7 +441,9 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     }
     if (lane < S) cs[lane] = DV ? tot[NW + lane] : Wsym(lane, 0);
     __syncwarp();
-    const double rk_sq = cs[0];
+    // c_0 = ||p_0||^2; the mixed form's FP32 p_0 carries the power-of-two scale of its outer
+    // iteration, which the stopping test between FP64 refreshes (check 2) takes out
+    const double rk_sq = gp.check == 2 ? cs[0] / (ctl->scale * ctl->scale) : cs[0];
     if (lane == 0) {
         int done = RUNNING;
         if (!(rk_sq >= 0.0) || !isfinite(rk_sq)) done = NUMERICAL;
@@ -659,12 +662,11 @@ int gram_occupancy_s(const GramArgs& g) {
     return (e == cudaSuccess && occ > 0) ? occ : 1;
 }
 
-template <int S>
-cudaError_t launch_gram_s(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st) {
+inline GramParams gram_params(const GramArgs& g) {
     GramParams gp{};
     gp.nu = g.nu;
     gp.solver = g.solver;
-    gp.check = g.fp32 ? 0 : 1;
+    gp.check = g.check;
     gp.theta = g.theta;
     gp.sigma = g.sigma;
     gp.dfac = g.dconst;
@@ -672,6 +674,12 @@ cudaError_t launch_gram_s(const GramArgs& g, double* partials, Ctl* ctl, int nbl
     gp.conj_nblk = g.conj_nblk;
     gp.conj_partials = g.conj_partials;
     gp.cj = g.cj;
+    return gp;
+}
+
+template <int S>
+cudaError_t launch_gram_s(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st) {
+    const GramParams gp = gram_params(g);
     const bool mom = g.form == SSTEP_GRAM_FORM_MOMENTS;
 #define SSTEP_GRAM_LAUNCH(DV, T, MOM, DIAG) \
     k_gram<S, DV, T, MOM><<<nblocks, GRAM_THREADS, 0, st>>>((const T*)g.P, g.ld, DIAG, g.n, partials, ctl, gp)
@@ -696,5 +704,82 @@ cudaError_t launch_gram_s(const GramArgs& g, double* partials, Ctl* ctl, int nbl
     return cudaGetLastError();
 }
 
+// Fused moments (gram_form FUSED): the s step kernels of an outer iteration left per-block
+// partials of a_j = <p_j, p_j> and b_j = <p_j, p_(j+1)>, j = 0 .. s-1 (unweighted: M = m I).
+// With A^ = theta (M^-1 A - sigma) self-adjoint in <., .>_M and p_j = T_j(A^) p_0, the
+// product rule 2 T_m T_n = T_(m+n) + T_|m-n| gives every moment mu_k = <p_0, T_k(A^) p_0>
+// (up to the constant m) from them: mu_0 = a_0, mu_1 = b_0, mu_2m = 2 a_m - mu_0 and
+// mu_(2m+1) = 2 b_m - mu_1, which is all the Gram system needs (k < 2s). Blocks sum fixed,
+// contiguous ranges of the partials in FP64 (FP32 partials: hi + lo converted exactly); the
+// last block to arrive sums the per-block results in block order (deterministic), lays the
+// moments out as the moments form's entries and runs the same scaling and solve.
+constexpr int FIN_THREADS = 512;
+constexpr int FIN_WARPS = FIN_THREADS / 32;
+
+template <int S, typename T>
+__global__ void __launch_bounds__(FIN_THREADS) k_moments_finish(const T* __restrict__ part, int nblk, double* part2,
+                                                               Ctl* ctl, GramParams gp) {
+    if (ctl->done) return;
+    constexpr int NV = 2 * S;                   // a_0, b_0, a_1, b_1, ...
+    constexpr int NC = sizeof(T) == 8 ? 1 : 2;  // components of one partial (FP32: hi, lo)
+    __shared__ double tot[NV];
+    __shared__ double ent[2 * S];
+    __shared__ double sm[2 * S * S + 4 * S];
+    __shared__ bool is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = gridDim.x;
+    const int lo = (int)((int64_t)nblk * blockIdx.x / R), hi = (int)((int64_t)nblk * (blockIdx.x + 1) / R);
+    for (int v = warp; v < NV; v += FIN_WARPS) {
+        // value v = (j, q): step j's partials start at j * 2 NC nblk, component c of q at
+        // (2 q + c) nblk (FP64: q nblk)
+        const int j = v >> 1, q = v & 1;
+        const T* base = part + (size_t)(2 * j + q) * NC * nblk;
+        double acc = 0.0;
+        for (int b = lo + lane; b < hi; b += 32) {
+            double x = (double)base[b];
+            if (NC == 2) x += (double)base[nblk + b];
+            acc += x;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) part2[(size_t)blockIdx.x * NV + v] = acc;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&ctl->counter, 1u) == (unsigned)R - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int v = warp; v < NV; v += FIN_WARPS) {
+        double acc = 0.0;
+        for (int r = lane; r < R; r += 32) acc += ((volatile double*)part2)[(size_t)r * NV + v];
+        acc = warp_sum(acc);
+        if (lane == 0) tot[v] = acc;
+    }
+    __syncthreads();
+    // entries in the layout of the moments form: e <= S: mu_e; S < e < 2S: <p_m, p_m> (e = 2m)
+    // or <p_m, p_(m+1)> (e = 2m + 1), from which gram_finish forms mu_e
+    for (int e = threadIdx.x; e < 2 * S; e += FIN_THREADS) {
+        const double am = tot[2 * (e >> 1)], bm = tot[2 * (e >> 1) + 1];   // a_(e/2), b_(e/2)
+        double v;
+        if (e <= 1) v = e == 0 ? tot[0] : tot[1];
+        else if (e <= S) v = (e % 2 == 0) ? 2.0 * am - tot[0] : 2.0 * bm - tot[1];
+        else v = (e % 2 == 0) ? am : bm;
+        ent[e] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ctl->counter = 0u;
+    if (warp == 0) gram_finish<S, false, true>(ent, gp, ctl, sm);
+}
+
+template <int S>
+cudaError_t launch_moments_finish_s(const GramArgs& g, const void* part, int nblk, double* part2, int nfin, Ctl* ctl,
+                                    cudaStream_t st) {
+    const GramParams gp = gram_params(g);
+    if (g.fp32)
+        k_moments_finish<S, float><<<nfin, FIN_THREADS, 0, st>>>((const float*)part, nblk, part2, ctl, gp);
+    else
+        k_moments_finish<S, double><<<nfin, FIN_THREADS, 0, st>>>((const double*)part, nblk, part2, ctl, gp);
+    return cudaGetLastError();
+}
 
 }  // namespace sstep

@@ -50,7 +50,7 @@ cudaError_t launch_grad_kappa(int dim, int nx, int ny, int nz, const double* kap
                               const double* lam, double* g, cudaStream_t st) {
     const int64_t n = (int64_t)nx * ny * nz;
     int64_t b = (n + AB - 1) / AB;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > 8 * (int64_t)device_sm_count()) b = 8 * (int64_t)device_sm_count();
     k_grad_kappa<<<(int)b, AB, 0, st>>>(dim, nx, ny, nz, kappa, x, lam, g);
     return cudaGetLastError();
 }

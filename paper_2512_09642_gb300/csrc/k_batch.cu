@@ -261,8 +261,8 @@ __global__ void k_batch_cond(cudaGraphConditionalHandle h, const int* running) {
     cudaGraphSetConditional(h, *running > 0 ? 1u : 0u);
 }
 
-int cap(int64_t items, int per_sm, int sms = 152) {
-    const int64_t c = (int64_t)per_sm * sms;
+int cap(int64_t items, int per_sm) {
+    const int64_t c = (int64_t)per_sm * device_sm_count();
     return (int)(items < 1 ? 1 : (items < c ? items : c));
 }
 

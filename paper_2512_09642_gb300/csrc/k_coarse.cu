@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(CF) k_coarse_fgs_formed(const double* __restri
 
 int grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
-    return (int)(b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b));
+    const int64_t c = 8 * (int64_t)device_sm_count();
+    return (int)(b < 1 ? 1 : (b > c ? c : b));
 }
 
 }  // namespace

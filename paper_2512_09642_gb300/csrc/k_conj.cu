@@ -176,7 +176,7 @@ cudaError_t launch_update_conj(int s, double* W, int64_t ld, int64_t n, const do
                                double theta, double sigma, const double* cj, double* x, const Ctl* ctl,
                                cudaStream_t st) {
     int64_t b = (n + UC - 1) / UC;
-    const int64_t cap = 152 * 4;
+    const int64_t cap = 4 * (int64_t)device_sm_count();
     const int nb = (int)(b < 1 ? 1 : (b < cap ? b : cap));
     const double h0 = 1.0 / theta, h1 = 0.5 / theta;
     const bool dv = diag != nullptr;

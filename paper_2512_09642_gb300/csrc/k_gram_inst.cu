@@ -10,4 +10,6 @@
 namespace sstep {
 template cudaError_t launch_gram_s<SSTEP_INST_S>(const GramArgs&, double*, Ctl*, int, cudaStream_t);
 template int gram_occupancy_s<SSTEP_INST_S>(const GramArgs&);
+template cudaError_t launch_moments_finish_s<SSTEP_INST_S>(const GramArgs&, const void*, int, double*, int, Ctl*,
+                                                           cudaStream_t);
 }  // namespace sstep

@@ -10,8 +10,11 @@
 //
 // The array (NOALLOC_SCRATCH_BYTES, about 224 KB) is part of the library image: every GPU
 // that loads the library holds it until the process exits. Its device address is looked up
-// once per device, on that device's first call (cudaGetSymbolAddress with the device
-// current); make that first call before any stream capture. Each device has its own copy,
+// per device with that device current (cudaGetSymbolAddress): on the device's first call, and
+// again on every call whose stream is not capturing, since a device reset reloads the module
+// and moves the array; a call made during stream capture uses the address of the device's
+// last call outside capture, so make a first call before any capture, and one after any
+// device reset before capturing again. Each device has its own copy,
 // so calls on different devices do not interact. On one device all calls share the array,
 // which keeps the last call's contents: each call first re-initialises the control block
 // (including the block-arrival counter, which must start at zero), and calls whose work can
@@ -59,13 +62,18 @@ __global__ void k_noalloc_init(Ctl* ctl) {
     ctl->scale_next = 1.0;
 }
 
+// Copies the results out of the shared control block. A solve that stopped early (numerical
+// breakdown) wrote none of them, so the scratch still holds an earlier call's values: the
+// outputs are then NaN, never another system's numbers.
 __global__ void k_noalloc_export(const Ctl* ctl, int s, double* out) {
+    const bool ok = ctl->done == RUNNING;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
     for (int i = threadIdx.x; i < s; i += blockDim.x) {
-        out[i] = ctl->alpha[i];
-        out[s + i] = ctl->d[i];
-        out[2 * s + i] = ctl->ct[i];
+        out[i] = ok ? ctl->alpha[i] : nan;
+        out[s + i] = ok ? ctl->d[i] : nan;
+        out[2 * s + i] = ok ? ctl->ct[i] : nan;
     }
-    for (int i = threadIdx.x; i < s * s; i += blockDim.x) out[3 * s + i] = ctl->Gt[i];
+    for (int i = threadIdx.x; i < s * s; i += blockDim.x) out[3 * s + i] = ok ? ctl->Gt[i] : nan;
     if (threadIdx.x == 0) out[3 * s + s * s] = (double)ctl->done;
 }
 
@@ -100,11 +108,22 @@ extern "C" sstep_status sstep_gram_fgs_noalloc(int64_t n, int s, int nu, int gra
     }
     unsigned char* base = nullptr;
     int sms = 0;
+    cudaStream_t st = (cudaStream_t)stream;
     {
         std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_scratch_addr[dev]) {
-            // one-time set-up on this device (it is current): the host-side symbol is only a
-            // stand-in, kernels need the device address
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cap);
+        if (e != cudaSuccess) {
+            set_global_error("sstep_gram_fgs_noalloc: cudaStreamIsCapturing failed");
+            return SSTEP_ERR_CUDA;
+        }
+        if (cap == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
+            if (cap != cudaStreamCaptureStatusNone) {
+                set_global_error("sstep_gram_fgs_noalloc: the first call on a device must come before stream capture");
+                return SSTEP_ERR_INVALID_ARG;
+            }
+            // this device is current: the host-side symbol is only a stand-in, kernels need the
+            // device address (looked up again outside capture: a device reset moves the array)
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_gram_scratch);
             if (e != cudaSuccess) {
@@ -123,7 +142,6 @@ extern "C" sstep_status sstep_gram_fgs_noalloc(int64_t n, int s, int nu, int gra
     }
     Ctl* ctl = (Ctl*)base;
     double* partials = (double*)(base + CTL_BYTES);
-    cudaStream_t st = (cudaStream_t)stream;
 
     const double theta = 2.0 / (lambda_max - lambda_min);
     const double sigma = 0.5 * (lambda_max + lambda_min);
@@ -141,6 +159,7 @@ extern "C" sstep_status sstep_gram_fgs_noalloc(int64_t n, int s, int nu, int gra
     g.ld = ldp;
     g.P = P_d;
     g.fp32 = false;
+    g.check = 1;
     int nblk = gram_blocks(g, sms < NOALLOC_MAX_BLOCKS ? sms : NOALLOC_MAX_BLOCKS);
     if (nblk > NOALLOC_MAX_BLOCKS) nblk = NOALLOC_MAX_BLOCKS;
 

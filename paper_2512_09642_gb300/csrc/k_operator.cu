@@ -24,6 +24,106 @@ constexpr int RB = 256;                      // CSR / vector kernels: threads pe
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// a + b written as fma(a, one, b) with one = 1 passed at run time (so the compiler cannot fold
+// it back into an add): the same correctly rounded sum, bit for bit, but this part issues FP64
+// FMAs at 627 G/s and FP64 adds at only 528 G/s (measured with independent chains at full
+// occupancy), so the FP64-pipe bound stencils run their additions as FMAs.
+template <typename T> __device__ __forceinline__ T add1(T a, T b, T one) { return fma(a, one, b); }
+
+// Fused moments (gram_form FUSED): the step that writes p_(j+1) also reduces a_j = <p_j, p_j>
+// and b_j = <p_j, p_(j+1)> (unweighted; M is a constant multiple of I), from which the Gram
+// finish forms every Chebyshev moment, so no pass re-reads the basis. Per-thread sums in the
+// step's precision (FP32: exact products summed as compensated pairs, Dot2), then a fixed
+// warp butterfly and a fixed order over the block's warps; one partial per block and value:
+// FP64 double[2][nblk] (a, b), FP32 float[4][nblk] (a_hi, a_lo, b_hi, b_lo). The FP32 form
+// adds no FP64 instruction to the step.
+template <typename T> struct MomAcc;
+template <> struct MomAcc<double> {
+    double a = 0.0, b = 0.0;
+    __device__ __forceinline__ void add(double pj, double pn) {
+        a = fma(pj, pj, a);
+        b = fma(pj, pn, b);
+    }
+};
+template <> struct MomAcc<float> {
+    float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+    __device__ __forceinline__ void add(float pj, float pn) {
+        dot2_acc(pj, pj, ah, al);
+        dot2_acc(pj, pn, bh, bl);
+    }
+};
+
+// (h, l) += (h2, l2): TwoSum on the high parts, the low parts and the error summed.
+__device__ __forceinline__ void pair_add(float& h, float& l, float h2, float l2) {
+    float t, e;
+    two_sum(h, h2, t, e);
+    h = t;
+    l = __fadd_rn(__fadd_rn(l, l2), e);
+}
+
+// Block reduction of the accumulators and the store of this block's partials. Every thread
+// of the block calls it (blocks of BX x BY threads, any grid shape).
+__device__ __forceinline__ void mom_block_store(const MomAcc<double>& m, void* part, int nblk) {
+    __shared__ double sh[BX * BY / 32][2];
+    const int t = threadIdx.x + BX * threadIdx.y, lane = t & 31, w = t >> 5;
+    // lanes of even index carry a, odd ones b after the first exchange: one FP64 add per level
+    double v = (lane & 1) ? m.b : m.a;
+    const double give = (lane & 1) ? m.a : m.b;
+    v += __shfl_xor_sync(0xffffffffu, give, 1);
+#pragma unroll
+    for (int o = 2; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane < 2) sh[w][lane] = v;
+    __syncthreads();
+    if (t < 2) {
+        double acc = sh[0][t];
+#pragma unroll
+        for (int k = 1; k < BX * BY / 32; ++k) acc += sh[k][t];
+        const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        ((double*)part)[(size_t)t * nblk + blk] = acc;
+    }
+}
+
+__device__ __forceinline__ void mom_block_store(const MomAcc<float>& m, void* part, int nblk) {
+    __shared__ float sh[BX * BY / 32][4];
+    const int t = threadIdx.x + BX * threadIdx.y, lane = t & 31, w = t >> 5;
+    float ah = m.ah, al = m.al, bh = m.bh, bl = m.bl;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pair_add(ah, al, __shfl_xor_sync(0xffffffffu, ah, o), __shfl_xor_sync(0xffffffffu, al, o));
+        pair_add(bh, bl, __shfl_xor_sync(0xffffffffu, bh, o), __shfl_xor_sync(0xffffffffu, bl, o));
+    }
+    if (lane == 0) {
+        sh[w][0] = ah;
+        sh[w][1] = al;
+        sh[w][2] = bh;
+        sh[w][3] = bl;
+    }
+    __syncthreads();
+    if (w == 0) {
+        // the block's warps, lane k holding warp k's pairs: a 3-level butterfly over lanes 0..7
+        constexpr int NW = BX * BY / 32;
+        static_assert(NW == 8, "the combine below assumes 8 warps per block");
+        const bool has = lane < NW;
+        ah = has ? sh[lane][0] : 0.f;
+        al = has ? sh[lane][1] : 0.f;
+        bh = has ? sh[lane][2] : 0.f;
+        bl = has ? sh[lane][3] : 0.f;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            pair_add(ah, al, __shfl_xor_sync(0xffffffffu, ah, o), __shfl_xor_sync(0xffffffffu, al, o));
+            pair_add(bh, bl, __shfl_xor_sync(0xffffffffu, bh, o), __shfl_xor_sync(0xffffffffu, bl, o));
+        }
+    }
+    if (t == 0) {
+        const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        float* pf = (float*)part;
+        pf[blk] = ah;
+        pf[(size_t)nblk + blk] = al;
+        pf[2 * (size_t)nblk + blk] = bh;
+        pf[3 * (size_t)nblk + blk] = bl;
+    }
+}
+
 
 // Face weights of the diffusion stencil in precision T.
 template <typename T> struct Faces { const T* wx; const T* wy; const T* wz; const T* diag; const T* cdinv; };
@@ -45,50 +145,56 @@ __device__ __forceinline__ T diffusion_offdiag_sum(const T* __restrict__ p, cons
 
 // Chebyshev step on a structured grid. POISSON: out = c1 p + c2 sum(nbrs) - q with the
 // constants folded on the host. Diffusion: out = c1 p - cdv_e s - q (Jacobi, cdv_e = c /
-// diag_e) or out = c ((diag_e - sigma) p - s) - q (no preconditioner).
-template <typename T, int DIM, bool POISSON, bool FIRST, bool JACOBI>
+// diag_e) or out = c ((diag_e - sigma) p - s) - q (no preconditioner). GRAM: also the fused
+// moments a_j, b_j of this block (mom: this step's partials, nblk blocks in the grid).
+template <typename T, int DIM, bool POISSON, bool JACOBI, bool FIRST, bool GRAM>
 __global__ void __launch_bounds__(BX* BY) k_cheb_stencil(const T* __restrict__ p, const T* __restrict__ q,
                                                          T* __restrict__ out, int nx, int ny, int nz, Faces<T> f,
-                                                         T c1, T c2, T csig, T cscale, const Ctl* __restrict__ ctl) {
+                                                         T c1, T c2, T csig, T cscale, const Ctl* __restrict__ ctl,
+                                                         T one, void* mom, int nblk) {
     if (ctl->done) return;
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
-    if (i >= nx || j >= ny) return;
-    const int64_t sxy = (int64_t)nx * ny;
-    const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
-    const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
-    int64_t e = i + (int64_t)nx * j + sxy * k0;
-    T pdn = (DIM == 3 && k0 > 0) ? ldg(p + e - sxy) : T(0);
-    T pc = ldg(p + e);
+    MomAcc<T> acc;
+    if (i < nx && j < ny) {
+        const int64_t sxy = (int64_t)nx * ny;
+        const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
+        const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+        int64_t e = i + (int64_t)nx * j + sxy * k0;
+        T pdn = (DIM == 3 && k0 > 0) ? ldg(p + e - sxy) : T(0);
+        T pc = ldg(p + e);
 #pragma unroll 2
-    for (int k = k0; k < k1; ++k, e += sxy) {
-        const T pup = (DIM == 3 && k < nz - 1) ? ldg(p + e + sxy) : T(0);
-        const T qv = FIRST ? T(0) : ldg(q + e);
-        T o;
-        if (POISSON) {
-            // neighbour sum as a depth-3 tree (x pair, y pair, z pair): same 5 adds, shorter chain
-            const T xm = (i > 0) ? ldg(p + e - 1) : T(0);
-            const T xp = (i < nx - 1) ? ldg(p + e + 1) : T(0);
-            const T ym = (j > 0) ? ldg(p + e - nx) : T(0);
-            const T yp = (j < ny - 1) ? ldg(p + e + nx) : T(0);
-            T s = (xm + xp) + (ym + yp);
-            if (DIM == 3) s += (k > 0 ? pdn : T(0)) + (k < nz - 1 ? pup : T(0));
-            o = FIRST ? fma(c2, s, c1 * pc) : fma(c2, s, fma(c1, pc, -qv));
-        } else {
-            const T s = diffusion_offdiag_sum<T, DIM>(p, f, e, i, j, k, nx, ny, nz, sxy, pdn, pup);
-            if (JACOBI) {
-                T cdv = ldg(f.cdinv + e);
-                if (FIRST) cdv *= cscale;
-                o = FIRST ? fma(-cdv, s, c1 * pc) : fma(-cdv, s, fma(c1, pc, -qv));
+        for (int k = k0; k < k1; ++k, e += sxy) {
+            const T pup = (DIM == 3 && k < nz - 1) ? ldg(p + e + sxy) : T(0);
+            const T qv = FIRST ? T(0) : ldg(q + e);
+            T o;
+            if (POISSON) {
+                // neighbour sum as a depth-3 tree (x pair, y pair, z pair): same 5 adds, shorter chain
+                const T xm = (i > 0) ? ldg(p + e - 1) : T(0);
+                const T xp = (i < nx - 1) ? ldg(p + e + 1) : T(0);
+                const T ym = (j > 0) ? ldg(p + e - nx) : T(0);
+                const T yp = (j < ny - 1) ? ldg(p + e + nx) : T(0);
+                T s = add1(add1(xm, xp, one), add1(ym, yp, one), one);
+                if (DIM == 3) s = add1(s, add1(k > 0 ? pdn : T(0), k < nz - 1 ? pup : T(0), one), one);
+                o = FIRST ? fma(c2, s, c1 * pc) : fma(c2, s, fma(c1, pc, -qv));
             } else {
-                const T t = fma(ldg(f.diag + e) - csig, pc, -s);
-                o = FIRST ? c1 * t : fma(c1, t, -qv);
+                const T s = diffusion_offdiag_sum<T, DIM>(p, f, e, i, j, k, nx, ny, nz, sxy, pdn, pup);
+                if (JACOBI) {
+                    T cdv = ldg(f.cdinv + e);
+                    if (FIRST) cdv *= cscale;
+                    o = FIRST ? fma(-cdv, s, c1 * pc) : fma(-cdv, s, fma(c1, pc, -qv));
+                } else {
+                    const T t = fma(ldg(f.diag + e) - csig, pc, -s);
+                    o = FIRST ? c1 * t : fma(c1, t, -qv);
+                }
             }
+            out[e] = o;
+            if (GRAM) acc.add(pc, o);
+            pdn = pc;
+            pc = pup;
         }
-        out[e] = o;
-        pdn = pc;
-        pc = pup;
     }
+    if (GRAM) mom_block_store(acc, mom, nblk);
 }
 
 // Poisson step with each thread on two x-adjacent points (nx even): 16-byte (8-byte in FP32)
@@ -100,10 +206,10 @@ template <typename T> struct Pair;
 template <> struct Pair<double> { using type = double2; };
 template <> struct Pair<float> { using type = float2; };
 
-template <typename T, int DIM, bool FIRST>
+template <typename T, int DIM, bool FIRST, bool GRAM>
 __global__ void __launch_bounds__(BX* BY) k_cheb_poisson_pair(const T* __restrict__ p, const T* __restrict__ q,
                                                               T* __restrict__ out, int nx, int ny, int nz, T c1, T c2,
-                                                              const Ctl* __restrict__ ctl) {
+                                                              const Ctl* __restrict__ ctl, T one, void* mom, int nblk) {
     if (ctl->done) return;
     using V = typename Pair<T>::type;
     const int lane = threadIdx.x;   // BX = 32: one warp per row of the tile
@@ -119,6 +225,7 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_poisson_pair(const T* __restric
     auto ld2 = [&](int64_t e) { return __ldg(reinterpret_cast<const V*>(p + e)); };
     V pdn = (DIM == 3 && in && k0 > 0) ? ld2(ij + sxy * (k0 - 1)) : zero;
     V pc = in ? ld2(ij + sxy * k0) : zero;
+    MomAcc<T> acc;
     for (int k = k0; k < k1; ++k) {
         const int64_t e = ij + sxy * k;
         const V pup = (DIM == 3 && in && k < nz - 1) ? ld2(e + sxy) : zero;
@@ -132,37 +239,91 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_poisson_pair(const T* __restric
         if (lane == 0) xl = (in && i0 > 0) ? ldg(p + e - 1) : T(0);
         if (lane == BX - 1) xr = (in && i + 2 < nx) ? ldg(p + e + 2) : T(0);
         if (in) {
-            T s0 = (xl + pc.y) + (ym.x + yp.x);
-            T s1 = (pc.x + xr) + (ym.y + yp.y);
+            T s0 = add1(add1(xl, pc.y, one), add1(ym.x, yp.x, one), one);
+            T s1 = add1(add1(pc.x, xr, one), add1(ym.y, yp.y, one), one);
             if (DIM == 3) {
-                s0 += pdn.x + pup.x;
-                s1 += pdn.y + pup.y;
+                s0 = add1(s0, add1(pdn.x, pup.x, one), one);
+                s1 = add1(s1, add1(pdn.y, pup.y, one), one);
             }
             V o;
             o.x = FIRST ? fma(c2, s0, c1 * pc.x) : fma(c2, s0, fma(c1, pc.x, -qv.x));
             o.y = FIRST ? fma(c2, s1, c1 * pc.y) : fma(c2, s1, fma(c1, pc.y, -qv.y));
             *reinterpret_cast<V*>(out + e) = o;
+            if (GRAM) {
+                acc.add(pc.x, o.x);
+                acc.add(pc.y, o.y);
+            }
         }
         pdn = pc;
         pc = pup;
     }
+    if (GRAM) mom_block_store(acc, mom, nblk);
 }
 
-// CSR Chebyshev step, one thread per row: y = A p, out = cdv (y) - c sigma p - q.
+// CSR rows, one per thread, in tiles of RB consecutive rows per block. The tile's nonzeros
+// (values and column indices, contiguous in memory) are first copied to shared memory with
+// coalesced loads - each warp request then covers whole cache lines, where a thread walking
+// its own row would make 32 requests scattered over the warp's rows - and every thread forms
+// its row's dot product from there, in the row's order (the FMA sequence of a plain row loop,
+// so the result is the same bit for bit). A tile with more than CSR_CAP nonzeros (rows much
+// longer than a stencil's) reads them from global memory instead.
+constexpr int CSR_CAP = 9 * RB;
+
+template <typename T> struct CsrTile {
+    T v[CSR_CAP];
+    int32_t c[CSR_CAP];
+};
+
+// (A p)_row for row = row0 + threadIdx.x (0 past the end). Called by every thread of the block
+// with the same row0; contains two block barriers.
+template <typename T>
+__device__ __forceinline__ T csr_tile_dot(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                          const T* __restrict__ vals, const T* __restrict__ p, int64_t n, int64_t row0,
+                                          CsrTile<T>& tile) {
+    const int t = threadIdx.x;
+    const int64_t row = row0 + t;
+    const int64_t rend = row0 + RB < n ? row0 + RB : n;
+    const int32_t b0 = ldg(rowptr + row0);
+    const int cnt = ldg(rowptr + rend) - b0;
+    const bool staged = cnt <= CSR_CAP;   // the same for the whole block
+    if (staged) {
+#pragma unroll 4
+        for (int k = t; k < cnt; k += RB) {
+            tile.v[k] = ldg(vals + b0 + k);
+            tile.c[k] = ldg(colind + b0 + k);
+        }
+    }
+    __syncthreads();
+    T y = T(0);
+    if (row < n) {
+        const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
+        if (staged) {
+            for (int k = s0 - b0; k < s1 - b0; ++k) y = fma(tile.v[k], ldg(p + tile.c[k]), y);
+        } else {
+            for (int32_t k = s0; k < s1; ++k) y = fma(ldg(vals + k), ldg(p + ldg(colind + k)), y);
+        }
+    }
+    __syncthreads();   // the next tile overwrites the shared copy
+    return y;
+}
+
+// CSR Chebyshev step: y = A p, out = cdv (y) - c sigma p - q.
 template <typename T, bool FIRST, bool JACOBI>
 __global__ void __launch_bounds__(RB) k_cheb_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                                                  const T* __restrict__ vals, const T* __restrict__ cdinv,
                                                  const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ out,
                                                  int64_t n, T c, T csig, T cscale, const Ctl* __restrict__ ctl) {
     if (ctl->done) return;
-    for (int64_t r = blockIdx.x * (int64_t)RB + threadIdx.x; r < n; r += (int64_t)gridDim.x * RB) {
-        const int32_t b = ldg(rowptr + r), en = ldg(rowptr + r + 1);
-        T y = T(0);
-        for (int32_t t = b; t < en; ++t) y = fma(ldg(vals + t), ldg(p + ldg(colind + t)), y);
-        T cdv = JACOBI ? ldg(cdinv + r) : c;
-        if (FIRST && JACOBI) cdv *= cscale;
-        const T pc = ldg(p + r);
-        out[r] = FIRST ? fma(cdv, y, -csig * pc) : fma(cdv, y, fma(-csig, pc, -ldg(q + r)));
+    __shared__ CsrTile<T> tile;
+    for (int64_t row0 = blockIdx.x * (int64_t)RB; row0 < n; row0 += (int64_t)gridDim.x * RB) {
+        const T y = csr_tile_dot<T>(rowptr, colind, vals, p, n, row0, tile);
+        const int64_t r = row0 + threadIdx.x;
+        if (r < n) {
+            T cdv = JACOBI ? ldg(cdinv + r) : c;
+            if (FIRST && JACOBI) cdv *= cscale;
+            const T pc = ldg(p + r);
+            out[r] = FIRST ? fma(cdv, y, -csig * pc) : fma(cdv, y, fma(-csig, pc, -ldg(q + r)));
+        }
     }
 }
 
@@ -245,7 +406,7 @@ template <int DIM, bool POISSON>
 __global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __restrict__ b, const double* __restrict__ x,
                                                              double* __restrict__ r, float* __restrict__ r32, int nx,
                                                              int ny, int nz, Faces<double> f, double d2,
-                                                             double* partials, Ctl* ctl, int mode) {
+                                                             double* partials, Ctl* ctl, int mode, double one) {
     if (mode == 2 && ctl->done) return;
     int kscale = 0;   // scale_next = 2^kscale
     if (mode == 2) {
@@ -268,19 +429,19 @@ __global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __res
             double ax;
             if (POISSON) {
                 double s = (i > 0) ? ldg(x + e - 1) : 0.0;
-                if (i < nx - 1) s += ldg(x + e + 1);
-                if (j > 0) s += ldg(x + e - nx);
-                if (j < ny - 1) s += ldg(x + e + nx);
+                if (i < nx - 1) s = add1(s, ldg(x + e + 1), one);
+                if (j > 0) s = add1(s, ldg(x + e - nx), one);
+                if (j < ny - 1) s = add1(s, ldg(x + e + nx), one);
                 if (DIM == 3) {
-                    if (k > 0) s += pdn;
-                    if (k < nz - 1) s += pup;
+                    if (k > 0) s = add1(s, pdn, one);
+                    if (k < nz - 1) s = add1(s, pup, one);
                 }
                 ax = fma(d2, pc, -s);
             } else {
                 const double s = diffusion_offdiag_sum<double, DIM>(x, f, e, i, j, k, nx, ny, nz, sxy, pdn, pup);
                 ax = fma(ldg(f.diag + e), pc, -s);
             }
-            const double rv = ldg(b + e) - ax;
+            const double rv = fma(ax, -one, ldg(b + e));   // b - ax
             if (r) r[e] = rv;
             if (r32) r32[e] = d2f_scaled(rv, kscale);
             ss = fma(rv, rv, ss);
@@ -313,14 +474,16 @@ __global__ void __launch_bounds__(RB) k_residual_csr(const int32_t* __restrict__
         kscale -= 1;
     }
     double ss = 0.0;
-    for (int64_t row = blockIdx.x * (int64_t)RB + threadIdx.x; row < n; row += (int64_t)gridDim.x * RB) {
-        const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
-        double y = 0.0;
-        for (int32_t t = s0; t < s1; ++t) y = fma(ldg(vals + t), ldg(x + ldg(colind + t)), y);
-        const double rv = ldg(b + row) - y;
-        if (r) r[row] = rv;
-        if (r32) r32[row] = d2f_scaled(rv, kscale);
-        ss = fma(rv, rv, ss);
+    __shared__ CsrTile<double> tile;
+    for (int64_t row0 = blockIdx.x * (int64_t)RB; row0 < n; row0 += (int64_t)gridDim.x * RB) {
+        const double y = csr_tile_dot<double>(rowptr, colind, vals, x, n, row0, tile);
+        const int64_t row = row0 + threadIdx.x;
+        if (row < n) {
+            const double rv = ldg(b + row) - y;
+            if (r) r[row] = rv;
+            if (r32) r32[row] = d2f_scaled(rv, kscale);
+            ss = fma(rv, rv, ss);
+        }
     }
     __shared__ double sh[RB / 32];
     const double tot = block_sum<RB>(ss, sh);
@@ -399,7 +562,7 @@ __device__ __forceinline__ BoxRegs<T> box_load(const T* __restrict__ p, int64_t 
 // S (the in-plane 3 x 3 box sum) at this thread's point from the plane held in v. Two block
 // barriers; sp / sr may be reused after it returns.
 template <typename T>
-__device__ __forceinline__ T box_plane_sum(T (*sp)[BX + 2], T (*sr)[BX], const BoxRegs<T>& v) {
+__device__ __forceinline__ T box_plane_sum(T (*sp)[BX + 2], T (*sr)[BX], const BoxRegs<T>& v, T one) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     sp[ty + 1][tx + 1] = v.c;
     if (tx == 0) sp[ty + 1][0] = v.hx;
@@ -408,17 +571,17 @@ __device__ __forceinline__ T box_plane_sum(T (*sp)[BX + 2], T (*sr)[BX], const B
     if (ty == BY - 1) sp[BY + 1][tx + 1] = v.hy;
     if (ty == 1 && tx < 4) sp[(tx >> 1) ? BY + 1 : 0][(tx & 1) ? BX + 1 : 0] = v.hc;
     __syncthreads();
-    sr[ty + 1][tx] = (sp[ty + 1][tx] + sp[ty + 1][tx + 1]) + sp[ty + 1][tx + 2];
-    if (ty == 0) sr[0][tx] = (sp[0][tx] + sp[0][tx + 1]) + sp[0][tx + 2];
-    if (ty == BY - 1) sr[BY + 1][tx] = (sp[BY + 1][tx] + sp[BY + 1][tx + 1]) + sp[BY + 1][tx + 2];
+    sr[ty + 1][tx] = add1(add1(sp[ty + 1][tx], sp[ty + 1][tx + 1], one), sp[ty + 1][tx + 2], one);
+    if (ty == 0) sr[0][tx] = add1(add1(sp[0][tx], sp[0][tx + 1], one), sp[0][tx + 2], one);
+    if (ty == BY - 1) sr[BY + 1][tx] = add1(add1(sp[BY + 1][tx], sp[BY + 1][tx + 1], one), sp[BY + 1][tx + 2], one);
     __syncthreads();
-    return (sr[ty][tx] + sr[ty + 1][tx]) + sr[ty + 2][tx];
+    return add1(add1(sr[ty][tx], sr[ty + 1][tx], one), sr[ty + 2][tx], one);
 }
 
 // Marches the block's tile over its z slab (3D: planes k0 .. k1 - 1; 2D: the one plane) and
 // calls emit(k, p_k, B_k, extra_k) for each, where extra_k = pre(k) was read one plane ahead.
 template <typename T, int DIM, typename Pre, typename Emit>
-__device__ __forceinline__ void box_march(const T* __restrict__ p, int nx, int ny, int nz, Pre pre, Emit emit) {
+__device__ __forceinline__ void box_march(const T* __restrict__ p, int nx, int ny, int nz, T one, Pre pre, Emit emit) {
     __shared__ T sp[BY + 2][BX + 2];
     __shared__ T sr[BY + 2][BX];
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
@@ -426,7 +589,7 @@ __device__ __forceinline__ void box_march(const T* __restrict__ p, int nx, int n
     if (DIM == 2) {
         const T ex = pre(0);
         const BoxRegs<T> v = box_load<T>(p, sxy, 0, true, i0, j0, nx, ny);
-        emit(0, v.c, box_plane_sum<T>(sp, sr, v), ex);
+        emit(0, v.c, box_plane_sum<T>(sp, sr, v, one), ex);
         return;
     }
     const int k0 = blockIdx.z * KB, k1 = min(nz, k0 + KB);
@@ -438,8 +601,8 @@ __device__ __forceinline__ void box_march(const T* __restrict__ p, int nx, int n
         const BoxRegs<T> nxt = box_load<T>(p, sxy, kk + 1, nvalid, i0, j0, nx, ny);
         const T ecur = (kk >= k0 && kk < k1) ? pre(kk) : T(0);
         const bool here = kk >= 0 && kk < nz;   // uniform over the block
-        const T sc = here ? box_plane_sum<T>(sp, sr, cur) : T(0);
-        if (kk - 1 >= k0) emit(kk - 1, pb, (sa + sb) + sc, eb);
+        const T sc = here ? box_plane_sum<T>(sp, sr, cur, one) : T(0);
+        if (kk - 1 >= k0) emit(kk - 1, pb, add1(add1(sa, sb, one), sc, one), eb);
         sa = sb;
         sb = sc;
         pb = cur.c;
@@ -448,70 +611,85 @@ __device__ __forceinline__ void box_march(const T* __restrict__ p, int nx, int n
     }
 }
 
-// Chebyshev step: out = ca p + cb B - q (q absent in the first step).
-template <typename T, int DIM, bool FIRST>
+// Chebyshev step: out = ca p + cb B - q (q absent in the first step); GRAM: with the fused
+// moments.
+template <typename T, int DIM, bool FIRST, bool GRAM>
 __global__ void __launch_bounds__(BX* BY) k_cheb_box(const T* __restrict__ p, const T* __restrict__ q,
                                                      T* __restrict__ out, int nx, int ny, int nz, T ca, T cb,
-                                                     const Ctl* __restrict__ ctl) {
+                                                     const Ctl* __restrict__ ctl, T one, void* mom, int nblk) {
     if (ctl->done) return;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const bool in = i < nx && j < ny;
     const int64_t ij = i + (int64_t)nx * j, sxy = (int64_t)nx * ny;
+    MomAcc<T> acc;
     box_march<T, DIM>(
-        p, nx, ny, nz, [&](int k) { return (FIRST || !in) ? T(0) : ldg(q + ij + sxy * k); },
+        p, nx, ny, nz, one, [&](int k) { return (FIRST || !in) ? T(0) : ldg(q + ij + sxy * k); },
         [&](int k, T pc, T B, T qv) {
-            if (in) out[ij + sxy * k] = FIRST ? fma(cb, B, ca * pc) : fma(cb, B, fma(ca, pc, -qv));
+            if (in) {
+                const T o = FIRST ? fma(cb, B, ca * pc) : fma(cb, B, fma(ca, pc, -qv));
+                out[ij + sxy * k] = o;
+                if (GRAM) acc.add(pc, o);
+            }
         });
+    if (GRAM) mom_block_store(acc, mom, nblk);
 }
 
 // FP32 box step (mixed form): the FP32 pipe has room for the plain 3 x 3 in-plane sums (9
 // loads through L1 and 8 adds per point and plane, the z-window of plane sums in registers),
 // which needs no shared memory and no barriers, so the kernel can run at the HBM rate.
-template <int DIM, bool FIRST>
+template <int DIM, bool FIRST, bool GRAM>
 __global__ void __launch_bounds__(BX* BY) k_cheb_box_f32(const float* __restrict__ p, const float* __restrict__ q,
                                                          float* __restrict__ out, int nx, int ny, int nz, float ca,
-                                                         float cb, const Ctl* __restrict__ ctl) {
+                                                         float cb, const Ctl* __restrict__ ctl, void* mom, int nblk) {
     if (ctl->done) return;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i >= nx || j >= ny) return;
-    const int64_t sxy = (int64_t)nx * ny, ij = i + (int64_t)nx * j;
-    const bool xm = i > 0, xp = i < nx - 1, ym = j > 0, yp = j < ny - 1;
-    auto row = [&](const float* a) { return ((xm ? ldg(a - 1) : 0.f) + ldg(a)) + (xp ? ldg(a + 1) : 0.f); };
-    auto plane = [&](int k, float& center) {   // 3 x 3 sum of plane k around (i, j)
-        const float* a = p + sxy * k + ij;
-        center = ldg(a);
-        const float r0 = ym ? row(a - nx) : 0.f;
-        const float r1 = ((xm ? ldg(a - 1) : 0.f) + center) + (xp ? ldg(a + 1) : 0.f);
-        const float r2 = yp ? row(a + nx) : 0.f;
-        return (r0 + r1) + r2;
-    };
-    if (DIM == 2) {
-        float pc;
-        const float S = plane(0, pc);
-        out[ij] = FIRST ? fmaf(cb, S, ca * pc) : fmaf(cb, S, fmaf(ca, pc, -ldg(q + ij)));
-        return;
+    MomAcc<float> acc;
+    if (i < nx && j < ny) {
+        const int64_t sxy = (int64_t)nx * ny, ij = i + (int64_t)nx * j;
+        const bool xm = i > 0, xp = i < nx - 1, ym = j > 0, yp = j < ny - 1;
+        auto row = [&](const float* a) { return ((xm ? ldg(a - 1) : 0.f) + ldg(a)) + (xp ? ldg(a + 1) : 0.f); };
+        auto plane = [&](int k, float& center) {   // 3 x 3 sum of plane k around (i, j)
+            const float* a = p + sxy * k + ij;
+            center = ldg(a);
+            const float r0 = ym ? row(a - nx) : 0.f;
+            const float r1 = ((xm ? ldg(a - 1) : 0.f) + center) + (xp ? ldg(a + 1) : 0.f);
+            const float r2 = yp ? row(a + nx) : 0.f;
+            return (r0 + r1) + r2;
+        };
+        if (DIM == 2) {
+            float pc;
+            const float S = plane(0, pc);
+            const float o = FIRST ? fmaf(cb, S, ca * pc) : fmaf(cb, S, fmaf(ca, pc, -ldg(q + ij)));
+            out[ij] = o;
+            if (GRAM) acc.add(pc, o);
+        } else {
+            const int k0 = blockIdx.z * KB, k1 = min(nz, k0 + KB);
+            float pc, ptmp;
+            float sdn = (k0 > 0) ? plane(k0 - 1, ptmp) : 0.f;
+            float sc = plane(k0, pc);
+            for (int k = k0; k < k1; ++k) {
+                float pup = 0.f, sup = 0.f;
+                if (k + 1 < nz) sup = plane(k + 1, pup);
+                const int64_t e = ij + sxy * k;
+                const float B = (sdn + sc) + sup;
+                const float o = FIRST ? fmaf(cb, B, ca * pc) : fmaf(cb, B, fmaf(ca, pc, -ldg(q + e)));
+                out[e] = o;
+                if (GRAM) acc.add(pc, o);
+                sdn = sc;
+                sc = sup;
+                pc = pup;
+            }
+        }
     }
-    const int k0 = blockIdx.z * KB, k1 = min(nz, k0 + KB);
-    float pc, ptmp;
-    float sdn = (k0 > 0) ? plane(k0 - 1, ptmp) : 0.f;
-    float sc = plane(k0, pc);
-    for (int k = k0; k < k1; ++k) {
-        float pup = 0.f, sup = 0.f;
-        if (k + 1 < nz) sup = plane(k + 1, pup);
-        const int64_t e = ij + sxy * k;
-        const float B = (sdn + sc) + sup;
-        out[e] = FIRST ? fmaf(cb, B, ca * pc) : fmaf(cb, B, fmaf(ca, pc, -ldg(q + e)));
-        sdn = sc;
-        sc = sup;
-        pc = pup;
-    }
+    if (GRAM) mom_block_store(acc, mom, nblk);
 }
 
 // r = b - A x = b - (3^d x - B) with ||r||^2 (residual modes as k_residual_stencil).
 template <int DIM>
 __global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restrict__ b, const double* __restrict__ x,
                                                          double* __restrict__ r, float* __restrict__ r32, int nx,
-                                                         int ny, int nz, double* partials, Ctl* ctl, int mode) {
+                                                         int ny, int nz, double* partials, Ctl* ctl, int mode,
+                                                         double one) {
     if (mode == 2 && ctl->done) return;
     int kscale = 0;   // scale_next = 2^kscale
     if (mode == 2) {
@@ -524,11 +702,11 @@ __global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restric
     const int64_t ij = i + (int64_t)nx * j, sxy = (int64_t)nx * ny;
     double ss = 0.0;
     box_march<double, DIM>(
-        x, nx, ny, nz, [&](int k) { return in ? ldg(b + ij + sxy * k) : 0.0; },
+        x, nx, ny, nz, one, [&](int k) { return in ? ldg(b + ij + sxy * k) : 0.0; },
         [&](int k, double pc, double B, double bv) {
             if (!in) return;
             const int64_t e = ij + sxy * k;
-            const double rv = bv - fma(dfull, pc, -B);
+            const double rv = fma(fma(dfull, pc, -B), -one, bv);   // bv - (dfull pc - B)
             if (r) r[e] = rv;
             if (r32) r32[e] = d2f_scaled(rv, kscale);
             ss = fma(rv, rv, ss);
@@ -553,7 +731,7 @@ __global__ void __launch_bounds__(BX* BY) k_apply_box(const double* __restrict__
     const bool in = i < nx && j < ny;
     const int64_t ij = i + (int64_t)nx * j, sxy = (int64_t)nx * ny;
     box_march<double, DIM>(
-        x, nx, ny, nz, [&](int) { return 0.0; },
+        x, nx, ny, nz, 1.0, [&](int) { return 0.0; },
         [&](int k, double pc, double B, double) {
             if (in) y[ij + sxy * k] = fma(dfull, pc, -B);
         });
@@ -566,11 +744,10 @@ dim3 box_grid(const OpDesc& op) {
 __global__ void __launch_bounds__(RB) k_apply_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                                                   const double* __restrict__ vals, const double* __restrict__ x,
                                                   double* __restrict__ y, int64_t n) {
-    for (int64_t row = blockIdx.x * (int64_t)RB + threadIdx.x; row < n; row += (int64_t)gridDim.x * RB) {
-        const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
-        double acc = 0.0;
-        for (int32_t t = s0; t < s1; ++t) acc = fma(ldg(vals + t), ldg(x + ldg(colind + t)), acc);
-        y[row] = acc;
+    __shared__ CsrTile<double> tile;
+    for (int64_t row0 = blockIdx.x * (int64_t)RB; row0 < n; row0 += (int64_t)gridDim.x * RB) {
+        const double acc = csr_tile_dot<double>(rowptr, colind, vals, x, n, row0, tile);
+        if (row0 + threadIdx.x < n) y[row0 + threadIdx.x] = acc;
     }
 }
 
@@ -578,9 +755,15 @@ dim3 stencil_grid(const OpDesc& op) {
     return dim3((op.nx + BX - 1) / BX, (op.ny + BY - 1) / BY, op.dim == 3 ? (op.nz + KC - 1) / KC : 1);
 }
 
+// two x-adjacent points per thread
+dim3 pair_grid(const OpDesc& op) {
+    const dim3 g = stencil_grid(op);
+    return dim3((op.nx + 2 * BX - 1) / (2 * BX), g.y, g.z);
+}
+
 int vec_blocks(int64_t n) {
     int64_t b = (n + RB - 1) / RB;
-    const int64_t cap = 152 * 8;
+    const int64_t cap = 8 * (int64_t)device_sm_count();
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
@@ -592,9 +775,30 @@ template <typename T> const T* csr_vals(const OpDesc& op);
 template <> const double* csr_vals<double>(const OpDesc& op) { return op.vals; }
 template <> const float* csr_vals<float>(const OpDesc& op) { return op.vals32; }
 
+// Launch of a step kernel K<..., FIRST, GRAM> with the fused-moments switch resolved at run time.
+#define SSTEP_STEP_LAUNCH(KERNEL, GRID, ...)                                                      \
+    do {                                                                                        \
+        const int nb_ = (int)((GRID).x * (GRID).y * (GRID).z);                                  \
+        if (first) {                                                                            \
+            if (mom) KERNEL<__VA_ARGS__, true, true><<<GRID, block, 0, st>>>(ARGS, mom, nb_);   \
+            else KERNEL<__VA_ARGS__, true, false><<<GRID, block, 0, st>>>(ARGS, nullptr, nb_);  \
+        } else {                                                                                \
+            if (mom) KERNEL<__VA_ARGS__, false, true><<<GRID, block, 0, st>>>(ARGS, mom, nb_);  \
+            else KERNEL<__VA_ARGS__, false, false><<<GRID, block, 0, st>>>(ARGS, nullptr, nb_); \
+        }                                                                                       \
+    } while (0)
+
+// Pair kernel for the Poisson stencil: nx even and the vectors 2-element aligned (the
+// workspace's always are), so every pair's loads and stores are aligned.
+template <typename T>
+bool use_pair(const OpDesc& op, const T* p, const T* q, const T* out) {
+    const size_t al = 2 * sizeof(T);
+    return op.nx % 2 == 0 && ((uintptr_t)p % al == 0) && ((uintptr_t)out % al == 0) && (!q || (uintptr_t)q % al == 0);
+}
+
 template <typename T, int DIM, bool POISSON>
 void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, double theta, double sigma, bool first,
-                           bool jacobi, const Ctl* ctl, cudaStream_t st) {
+                           bool jacobi, const Ctl* ctl, void* mom, cudaStream_t st) {
     const dim3 grid = stencil_grid(op), block(BX, BY);
     const double c = first ? theta : 2.0 * theta;
     const Faces<T> f = faces_of<T>(op);
@@ -602,51 +806,53 @@ void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, dou
         // D^-1 A p - sigma p = (1 - sigma) p - sum / (2 dim) with Jacobi (D = 2 dim I);
         // A p - sigma p = (2 dim - sigma) p - sum without.
         const double d2 = 2.0 * op.dim;
-        const double c1 = jacobi ? c * (1.0 - sigma) : c * (d2 - sigma);
-        const double c2 = jacobi ? -c / d2 : -c;
-        // pair kernel: with nx even every pair starts at an even index, so its 2-element loads
-        // and stores are aligned when the columns are (the workspace's always are)
-        const size_t al = 2 * sizeof(T);
-        const bool aligned = ((uintptr_t)p % al == 0) && ((uintptr_t)out % al == 0) && (!q || (uintptr_t)q % al == 0);
-        if (op.nx % 2 == 0 && aligned) {
-            const dim3 g2((op.nx + 2 * BX - 1) / (2 * BX), grid.y, grid.z);
-            if (first)
-                k_cheb_poisson_pair<T, DIM, true><<<g2, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, (T)c1, (T)c2, ctl);
-            else
-                k_cheb_poisson_pair<T, DIM, false><<<g2, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, (T)c1, (T)c2, ctl);
+        const T c1 = (T)(jacobi ? c * (1.0 - sigma) : c * (d2 - sigma));
+        const T c2 = (T)(jacobi ? -c / d2 : -c);
+        if (use_pair(op, p, q, out)) {
+            const dim3 g2 = pair_grid(op);
+#define ARGS p, q, out, op.nx, op.ny, op.nz, c1, c2, ctl, T(1)
+            SSTEP_STEP_LAUNCH(k_cheb_poisson_pair, g2, T, DIM);
+#undef ARGS
             return;
         }
-        if (first)
-            k_cheb_stencil<T, DIM, true, true, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f, (T)c1,
-                                                                           (T)c2, T(0), T(1), ctl);
-        else
-            k_cheb_stencil<T, DIM, true, false, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f, (T)c1,
-                                                                            (T)c2, T(0), T(1), ctl);
+#define ARGS p, q, out, op.nx, op.ny, op.nz, f, c1, c2, T(0), T(1), ctl, T(1)
+        SSTEP_STEP_LAUNCH(k_cheb_stencil, grid, T, DIM, true, true);
+#undef ARGS
         return;
     }
     if (jacobi) {
-        const double c1 = c * (1.0 - sigma);
-        if (first)
-            k_cheb_stencil<T, DIM, false, true, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f,
-                                                                            (T)c1, T(0), T(0), T(0.5), ctl);
-        else
-            k_cheb_stencil<T, DIM, false, false, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f,
-                                                                             (T)c1, T(0), T(0), T(1), ctl);
+        const T c1 = (T)(c * (1.0 - sigma));
+        const T csc = first ? T(0.5) : T(1);
+#define ARGS p, q, out, op.nx, op.ny, op.nz, f, c1, T(0), T(0), csc, ctl, T(1)
+        SSTEP_STEP_LAUNCH(k_cheb_stencil, grid, T, DIM, false, true);
+#undef ARGS
     } else {
-        if (first)
-            k_cheb_stencil<T, DIM, false, true, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f,
-                                                                             (T)c, T(0), (T)sigma, T(1), ctl);
-        else
-            k_cheb_stencil<T, DIM, false, false, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, f,
-                                                                              (T)c, T(0), (T)sigma, T(1), ctl);
+        const T cc = (T)c, cs = (T)sigma;
+#define ARGS p, q, out, op.nx, op.ny, op.nz, f, cc, T(0), cs, T(1), ctl, T(1)
+        SSTEP_STEP_LAUNCH(k_cheb_stencil, grid, T, DIM, false, false);
+#undef ARGS
     }
 }
 
 }  // namespace
 
+int cheb_step_blocks(const OpDesc& op) {
+    if (op.kind != OP_STENCIL) return 0;
+    dim3 g;
+    if (op.box) g = box_grid(op);
+    else if (op.wx == nullptr && op.nx % 2 == 0) g = pair_grid(op);
+    else g = stencil_grid(op);
+    return (int)(g.x * g.y * g.z);
+}
+
 template <typename T>
 cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, double theta, double sigma, bool first,
-                             bool jacobi, const Ctl* ctl, cudaStream_t st) {
+                             bool jacobi, const Ctl* ctl, cudaStream_t st, void* mom) {
+    if (mom) {
+        // the fused moments need a stencil operator and the block count cheb_step_blocks reports
+        if (op.kind != OP_STENCIL) return cudaErrorInvalidValue;
+        if (!op.box && op.wx == nullptr && op.nx % 2 == 0 && !use_pair(op, p, q, out)) return cudaErrorInvalidValue;
+    }
     if (op.kind == OP_STENCIL && op.box) {
         // c (M^-1 A p - sigma p) = c (D + 1 - sigma) p - c B without a preconditioner and
         // c (1 - sigma + 1 / D) p - (c / D) B with Jacobi (D = 3^dim - 1)
@@ -659,32 +865,27 @@ cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, d
             const float* pf = (const float*)p;
             const float* qf = (const float*)q;
             float* of = (float*)out;
-            if (op.dim == 3) {
-                if (first) k_cheb_box_f32<3, true><<<grid, block, 0, st>>>(pf, qf, of, op.nx, op.ny, op.nz, (float)ca, (float)cb, ctl);
-                else k_cheb_box_f32<3, false><<<grid, block, 0, st>>>(pf, qf, of, op.nx, op.ny, op.nz, (float)ca, (float)cb, ctl);
-            } else {
-                if (first) k_cheb_box_f32<2, true><<<grid, block, 0, st>>>(pf, qf, of, op.nx, op.ny, op.nz, (float)ca, (float)cb, ctl);
-                else k_cheb_box_f32<2, false><<<grid, block, 0, st>>>(pf, qf, of, op.nx, op.ny, op.nz, (float)ca, (float)cb, ctl);
-            }
+            const float caf = (float)ca, cbf = (float)cb;
+#define ARGS pf, qf, of, op.nx, op.ny, op.nz, caf, cbf, ctl
+            if (op.dim == 3) SSTEP_STEP_LAUNCH(k_cheb_box_f32, grid, 3);
+            else SSTEP_STEP_LAUNCH(k_cheb_box_f32, grid, 2);
+#undef ARGS
             return cudaGetLastError();
         }
-        if (op.dim == 3) {
-            if (first) k_cheb_box<T, 3, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
-            else k_cheb_box<T, 3, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
-        } else {
-            if (first) k_cheb_box<T, 2, true><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
-            else k_cheb_box<T, 2, false><<<grid, block, 0, st>>>(p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl);
-        }
+#define ARGS p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl, T(1)
+        if (op.dim == 3) SSTEP_STEP_LAUNCH(k_cheb_box, grid, T, 3);
+        else SSTEP_STEP_LAUNCH(k_cheb_box, grid, T, 2);
+#undef ARGS
         return cudaGetLastError();
     }
     if (op.kind == OP_STENCIL) {
         const bool poisson = op.wx == nullptr;
         if (op.dim == 3) {
-            if (poisson) cheb_stencil_dispatch<T, 3, true>(op, p, q, out, theta, sigma, first, jacobi, ctl, st);
-            else cheb_stencil_dispatch<T, 3, false>(op, p, q, out, theta, sigma, first, jacobi, ctl, st);
+            if (poisson) cheb_stencil_dispatch<T, 3, true>(op, p, q, out, theta, sigma, first, jacobi, ctl, mom, st);
+            else cheb_stencil_dispatch<T, 3, false>(op, p, q, out, theta, sigma, first, jacobi, ctl, mom, st);
         } else {
-            if (poisson) cheb_stencil_dispatch<T, 2, true>(op, p, q, out, theta, sigma, first, jacobi, ctl, st);
-            else cheb_stencil_dispatch<T, 2, false>(op, p, q, out, theta, sigma, first, jacobi, ctl, st);
+            if (poisson) cheb_stencil_dispatch<T, 2, true>(op, p, q, out, theta, sigma, first, jacobi, ctl, mom, st);
+            else cheb_stencil_dispatch<T, 2, false>(op, p, q, out, theta, sigma, first, jacobi, ctl, mom, st);
         }
         return cudaGetLastError();
     }
@@ -701,11 +902,12 @@ cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, d
     }
     return cudaGetLastError();
 }
+#undef SSTEP_STEP_LAUNCH
 
 template cudaError_t launch_cheb_step<double>(const OpDesc&, const double*, const double*, double*, double, double,
-                                              bool, bool, const Ctl*, cudaStream_t);
+                                              bool, bool, const Ctl*, cudaStream_t, void*);
 template cudaError_t launch_cheb_step<float>(const OpDesc&, const float*, const float*, float*, double, double, bool,
-                                             bool, const Ctl*, cudaStream_t);
+                                             bool, const Ctl*, cudaStream_t, void*);
 
 size_t residual_partials_needed(const OpDesc& op) {
     if (op.kind == OP_STENCIL && op.box) {
@@ -723,8 +925,8 @@ cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, 
                             double* partials, Ctl* ctl, int mode, cudaStream_t st) {
     if (op.kind == OP_STENCIL && op.box) {
         const dim3 grid = box_grid(op), block(BX, BY);
-        if (op.dim == 3) k_residual_box<3><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode);
-        else k_residual_box<2><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode);
+        if (op.dim == 3) k_residual_box<3><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode, 1.0);
+        else k_residual_box<2><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode, 1.0);
         return cudaGetLastError();
     }
     if (op.kind == OP_STENCIL) {
@@ -733,11 +935,11 @@ cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, 
         const double d2 = 2.0 * op.dim;
         const bool poisson = op.wx == nullptr;
         if (op.dim == 3) {
-            if (poisson) k_residual_stencil<3, true><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
-            else k_residual_stencil<3, false><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
+            if (poisson) k_residual_stencil<3, true><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode, 1.0);
+            else k_residual_stencil<3, false><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode, 1.0);
         } else {
-            if (poisson) k_residual_stencil<2, true><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
-            else k_residual_stencil<2, false><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode);
+            if (poisson) k_residual_stencil<2, true><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode, 1.0);
+            else k_residual_stencil<2, false><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, f, d2, partials, ctl, mode, 1.0);
         }
         return cudaGetLastError();
     }

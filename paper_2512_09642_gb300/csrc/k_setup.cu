@@ -4,13 +4,27 @@
 #include "kernels.h"
 
 namespace sstep {
+
+int device_sm_count() {
+    constexpr int MAXDEV = 64;
+    static int cache[MAXDEV] = {};   // a benign race: every writer stores the same value
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return 152;
+    if (cache[dev] <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
 namespace {
 
 constexpr int TB = 256;
 
 int nblocks(int64_t n) {
-    const int64_t b = (n + TB - 1) / TB;
-    return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
+    const int64_t b = (n + TB - 1) / TB, cap = 8 * (int64_t)device_sm_count();
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 __global__ void k_csr_diag(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,

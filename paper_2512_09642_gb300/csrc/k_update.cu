@@ -37,34 +37,41 @@ __global__ void __launch_bounds__(UB) k_update_f64(const double* __restrict__ P,
     }
 }
 
-// Mixed form (FP32 basis p^_j = scale * p_j): x += (sum_j alpha_j p^_j) / scale. alpha_j is
-// split into FP32 hi + lo; the sum over j is a compensated FP32 dot product (about 44
-// significant bits) taken in the scaled domain, where its terms are O(1), and added to x in
-// FP64 through exact conversions: one add and one FMA on the FP64 pipe per unknown.
-template <int S>
-__global__ void __launch_bounds__(UB) k_update_mixed(const float* __restrict__ P, int64_t ld, int64_t n,
-                                                     double* __restrict__ x, const Ctl* __restrict__ ctl) {
+// Mixed form (FP32 basis p^_j = scale * p_j): x += (sum_j alpha_j p^_j) / scale, the sum
+// taken in FP32 in the scaled domain (where its terms are O(1)) with alpha rounded to FP32, and
+// added to x in FP64 through an exact conversion (one FMA on the FP64 pipe per unknown). The
+// increment only has to be accurate relative to itself: its FP32 rounding (about 1e-7 of the
+// terms) is part of the next residual, which the FP64 refresh r = b - A x recomputes, as in
+// iterative refinement.
+// WR (the next outer iteration does not refresh): also the recursive residual in the same
+// scaled domain, written over p^_0 in FP32: r^ = sum_k gamma_k p^_k (constant M) or
+// r^ = p^_0 - d (sum_k beta_k p^_k) (vector M = diag d). Its FP32 rounding drifts from
+// b - A x until the next refresh, which restores it.
+template <int S, bool WR, bool DV>
+__global__ void __launch_bounds__(UB) k_update_mixed(float* __restrict__ P, int64_t ld, int64_t n,
+                                                     double* __restrict__ x, const float* __restrict__ diag,
+                                                     const Ctl* __restrict__ ctl) {
     if (ctl->done) return;
-    __shared__ float ah[S], al[S];
-    if (threadIdx.x < S) {
-        const double a = ctl->alpha[threadIdx.x];
-        const float h = __double2float_rn(a);
-        ah[threadIdx.x] = h;
-        al[threadIdx.x] = __double2float_rn(a - (double)h);
-    }
+    __shared__ float af[S], gf[S + 1];
+    if (threadIdx.x < S) af[threadIdx.x] = __double2float_rn(ctl->alpha[threadIdx.x]);
+    if (WR && threadIdx.x <= S) gf[threadIdx.x] = __double2float_rn(ctl->beta[threadIdx.x]);
     __syncthreads();
     const double inv_scale = 1.0 / ctl->scale;   // exact: scale is a power of two
+    constexpr int NC = WR ? S + 1 : S;
     for (int64_t e = blockIdx.x * (int64_t)UB + threadIdx.x; e < n; e += (int64_t)gridDim.x * UB) {
-        float pv[S];
+        float pv[NC];
 #pragma unroll
-        for (int j = 0; j < S; ++j) pv[j] = __ldg(P + j * ld + e);   // all loads in flight first
-        float sh = 0.f, sl = 0.f;
+        for (int j = 0; j < NC; ++j) pv[j] = __ldg(P + j * ld + e);   // all loads in flight first
+        float sx = 0.f;
 #pragma unroll
-        for (int j = 0; j < S; ++j) {
-            dot2_acc(ah[j], pv[j], sh, sl);
-            sl = fmaf(al[j], pv[j], sl);
+        for (int j = 0; j < S; ++j) sx = fmaf(af[j], pv[j], sx);
+        x[e] = fma(f2d_exact(sx), inv_scale, x[e]);
+        if (WR) {
+            float sr = 0.f;
+#pragma unroll
+            for (int k = 0; k <= S; ++k) sr = fmaf(gf[k], pv[k], sr);
+            P[e] = DV ? fmaf(-__ldg(diag + e), sr, pv[0]) : sr;
         }
-        x[e] = fma(f2d_exact(sh) + f2d_exact(sl), inv_scale, x[e]);
     }
 }
 
@@ -77,7 +84,7 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle handle, const Ctl* __rest
 // 4, the HBM-bound mixed update with 8 in flight), fewer for short vectors.
 int blocks_for(int64_t n, int per_sm) {
     const int64_t b = (n + UB - 1) / UB;
-    const int64_t cap = 152 * (int64_t)per_sm;
+    const int64_t cap = (int64_t)device_sm_count() * per_sm;
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
@@ -88,11 +95,16 @@ cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
-                                cudaStream_t st) {
+cudaError_t launch_update_mixed(float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl, cudaStream_t st,
+                                bool write_r, const float* diag) {
     const int nb = blocks_for(n, 8);
     switch (s) {
-#define SSTEP_CASE(S) case S: k_update_mixed<S><<<nb, UB, 0, st>>>(P, ld, n, x, ctl); break;
+#define SSTEP_CASE(S)                                                                                  \
+    case S:                                                                                            \
+        if (!write_r) k_update_mixed<S, false, false><<<nb, UB, 0, st>>>(P, ld, n, x, nullptr, ctl);    \
+        else if (diag) k_update_mixed<S, true, true><<<nb, UB, 0, st>>>(P, ld, n, x, diag, ctl);        \
+        else k_update_mixed<S, true, false><<<nb, UB, 0, st>>>(P, ld, n, x, nullptr, ctl);              \
+        break;
         SSTEP_CASE(1) SSTEP_CASE(2) SSTEP_CASE(3) SSTEP_CASE(4) SSTEP_CASE(5) SSTEP_CASE(6) SSTEP_CASE(7)
         SSTEP_CASE(8) SSTEP_CASE(9) SSTEP_CASE(10) SSTEP_CASE(11) SSTEP_CASE(12) SSTEP_CASE(13) SSTEP_CASE(14)
         SSTEP_CASE(15) SSTEP_CASE(16) SSTEP_CASE(17) SSTEP_CASE(18) SSTEP_CASE(19) SSTEP_CASE(20) SSTEP_CASE(21)

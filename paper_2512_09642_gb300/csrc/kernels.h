@@ -34,10 +34,16 @@ enum { OP_CSR = 0, OP_STENCIL = 1 };
 
 // One Chebyshev step (Section 2, Definition): out = c (M^-1 A p - sigma p) - q,
 // c = theta for the first step (q absent) and 2 theta after. `first` selects the form.
-// Precision T = double (FP64) or float (mixed form basis).
+// Precision T = double (FP64) or float (mixed form basis). mom != null (stencil operators
+// only): the step also writes its per-block partials of <p, p> and <p, out> there (the fused
+// moments of gram_form FUSED; FP64 double[2][nblk], FP32 float[4][nblk] with nblk =
+// cheb_step_blocks(op)).
 template <typename T>
 cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, double theta,
-                             double sigma, bool first, bool jacobi, const Ctl* ctl, cudaStream_t st);
+                             double sigma, bool first, bool jacobi, const Ctl* ctl, cudaStream_t st,
+                             void* mom = nullptr);
+// Blocks of the stencil step kernel launch_cheb_step uses for op (0 for CSR).
+int cheb_step_blocks(const OpDesc& op);
 
 // r = b - A x in FP64; writes r (double, if non-null) and, if r32 != null, the FP32 copy
 // scaled by ctl->scale_next (mode 2); reduces ||r||^2 through `partials` (one double per
@@ -58,6 +64,9 @@ cudaError_t launch_apply(const OpDesc& op, const double* x, double* y, cudaStrea
 // columns at stride ld). Per-block partials go to `partials` (gram_partials_needed doubles).
 struct GramArgs {
     int s, nu, solver, form;
+    // stopping test in the Gram finish: 0 none (the mixed form's FP64 refresh tests), 1 on
+    // c_0 = ||r_k||^2, 2 on c_0 / scale^2 (mixed form, outer iterations without a refresh)
+    int check;
     double theta, sigma;
     bool dvec;                 // D is the vector op.diag (else the constant op.dconst)
     double dconst;
@@ -73,6 +82,13 @@ struct GramArgs {
     double* cj;
 };
 cudaError_t launch_gram(const GramArgs& g, double* partials, Ctl* ctl, int nblocks, cudaStream_t st);
+// Gram finish of the fused moments form: sums the s step kernels' partials (part, nblk blocks
+// per step, layout of launch_cheb_step's mom) through part2 (moments_finish_blocks(nblk) x 2s
+// doubles) and runs the column scaling and Gram solve (M = g.dconst I).
+constexpr int MAX_FIN_BLOCKS = 64;
+int moments_finish_blocks(int nblk);
+cudaError_t launch_moments_finish(const GramArgs& g, const void* part, int nblk, double* part2, Ctl* ctl,
+                                  cudaStream_t st);
 int gram_blocks(const GramArgs& g, int sm_count);
 size_t gram_partials_needed(const GramArgs& g, int nblocks);
 
@@ -88,9 +104,10 @@ struct UpdateArgs {
     bool skip_r;
 };
 cudaError_t launch_update(const UpdateArgs& u, const Ctl* ctl, cudaStream_t st);
-// Mixed form: x += P alpha / scale with FP32 P (compensated FP32 sum, exact FP64 add-in).
-cudaError_t launch_update_mixed(const float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl,
-                                cudaStream_t st);
+// Mixed form: x += P alpha / scale with FP32 P (compensated FP32 sum, exact FP64 add-in);
+// write_r: also the recursive FP32 residual over column 0 (diag: the vector M, else M const).
+cudaError_t launch_update_mixed(float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl, cudaStream_t st,
+                                bool write_r, const float* diag);
 
 // Block-conjugated form (FP64, s <= 16). The workspace holds, at stride ld, the columns
 // P_+ = [p_0 .. p_s] (0 .. s), Q_(k-1) (s+1 .. 2s) and A Q_(k-1) (2s+1 .. 3s).
@@ -119,6 +136,10 @@ cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, 
 // Adjoint: dL/dkappa of the diffusion stencil from x and lambda (see k_adjoint.cu).
 cudaError_t launch_grad_kappa(int dim, int nx, int ny, int nz, const double* kappa, const double* x,
                               const double* lam, double* g, cudaStream_t st);
+
+// Streaming multiprocessors of the current device (queried once per device; the launchers
+// size their grids as a multiple of it).
+int device_sm_count();
 
 // Setup kernels.
 cudaError_t launch_csr_diag(const OpDesc& op, double* diag, int* bad, cudaStream_t st);

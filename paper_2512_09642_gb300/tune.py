@@ -1,5 +1,7 @@
 """Autotuner for the batched form: picks s, nu, the Gram form and the launch shapes (unknowns
-per Gram/update work item, resident blocks per SM of the stencil kernels) for a given batch.
+per Gram/update work item, resident blocks per SM of the stencil kernels) for a given batch,
+in two stages: (s, nu, Gram form) over DEFAULT_CANDIDATES at the default shapes, then the
+launch shapes over SHAPE_CANDIDATES at the chosen (s, nu, form).
 
 For each candidate it solves a subsample of the batch to the tolerance with the library's
 batched solve (the largest systems, which set the batch's critical path, plus a spread of
@@ -28,6 +30,10 @@ DEFAULT_CANDIDATES = [
     for (s, nu) in ((6, 20), (8, 20), (8, 30), (10, 25), (12, 30))
     for form in ("direct", "moments")
 ]
+
+
+SHAPE_CANDIDATES = [{"batch_chunk": chunk, "batch_ctas_per_sm": ctas}
+                    for chunk in (4096, 8192, 16384) for ctas in (4, 6, 8)]
 
 
 @dataclass
@@ -66,9 +72,11 @@ def _solve_sample(grids, kappas, bs, cand: dict, tol: float, max_outer: int, str
 
 
 def tune(grids, kappas, bs, tol: float = 1e-8, candidates: Optional[list] = None, sample: int = 12,
-         max_outer: int = 40000, stream=None) -> TuneResult:
-    """grids: list of (nx, ny[, nz]); kappas: CUDA tensors or None; bs: CUDA right-hand sides."""
+         max_outer: int = 40000, stream=None, shapes: Optional[list] = None) -> TuneResult:
+    """grids: list of (nx, ny[, nz]); kappas: CUDA tensors or None; bs: CUDA right-hand sides.
+    shapes: launch shapes of the second stage (SHAPE_CANDIDATES by default; [] skips it)."""
     candidates = candidates or DEFAULT_CANDIDATES
+    shapes = SHAPE_CANDIDATES if shapes is None else shapes
     sizes = np.array([int(np.prod(g)) for g in grids], dtype=np.float64)
     idx = pick_sample(list(sizes), sample)
     sg = [grids[i] for i in idx]
@@ -76,7 +84,8 @@ def tune(grids, kappas, bs, tol: float = 1e-8, candidates: Optional[list] = None
     sb = [bs[i] for i in idx]
     n_s = sizes[idx]
     table = []
-    for cand in candidates:
+
+    def run(cand, stage):
         ms, outers, status = _solve_sample(sg, sk, sb, cand, tol, max_outer, stream)
         N = np.maximum(np.asarray(outers, dtype=np.float64), 1.0)
         ok = all(st == "SSTEP_OK" for st in status)
@@ -85,8 +94,21 @@ def tune(grids, kappas, bs, tol: float = 1e-8, candidates: Optional[list] = None
         N_all = np.exp(a_) * sizes ** b_
         c = ms / float(np.sum(n_s * N))                      # ms per unknown-outer on the sample
         pred = c * float(np.sum(sizes * N_all)) / 1e3
-        table.append(dict(cand, sample_ms=ms, fit_exponent=float(b_), predicted_s=pred if ok else float("inf"),
-                          sample_max_outer=int(N.max())))
+        row = dict(cand, stage=stage, sample_ms=ms, fit_exponent=float(b_),
+                   predicted_s=pred if ok else float("inf"), sample_max_outer=int(N.max()),
+                   ns_per_unknown_outer=c * 1e6)
+        table.append(row)
+        return row
+
+    for cand in candidates:
+        run(cand, "basis")
     best = min(table, key=lambda r: r["predicted_s"])
-    params = {k: best[k] for k in ("s", "nu", "gram_form", "batch_chunk", "batch_ctas_per_sm")}
+    keys = ("s", "nu", "gram_form", "batch_chunk", "batch_ctas_per_sm")
+    for shape in shapes:
+        cand = dict({k: best[k] for k in keys}, **shape)
+        if any(all(r[k] == cand[k] for k in keys) for r in table):
+            continue   # this shape was measured in the first stage
+        run(cand, "shape")
+    best = min(table, key=lambda r: r["predicted_s"])
+    params = {k: best[k] for k in keys}
     return TuneResult(best=params, predicted_s=best["predicted_s"], table=table, sample=idx)

@@ -7,6 +7,12 @@ take hours on one CPU core, which is why their results are stored.
 
     python tests/golden/make_oracle_outer_counts.py [sides...]
     python tests/golden/make_oracle_outer_counts.py box [sides...]
+    python tests/golden/make_oracle_outer_counts.py seeds [side]
+
+`seeds` writes tests/golden/oracle_outer_counts_seeds.txt: the 7-point Poisson problem at one
+side (default 128) for the five exact solutions x* of seeds 1002, 1102, 1202, 1302 and 1402
+(1002 is the benchmark's), solved in parallel worker processes. It measures how much the
+literal restarted iteration's outer-iteration count depends on the right-hand side.
 """
 import os
 import sys
@@ -21,6 +27,8 @@ from workloads import problems as W  # noqa: E402
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "oracle_outer_counts.txt")
 OUT_BOX = os.path.join(HERE, "oracle_outer_counts_box.txt")
+OUT_SEEDS = os.path.join(HERE, "oracle_outer_counts_seeds.txt")
+SPREAD_SEEDS = (1002, 1102, 1202, 1302, 1402)
 
 
 def run(name, p, s, nu, bounds="gersh_lanczos10"):
@@ -45,7 +53,26 @@ def main_box(sides):
             f.write("\n".join(lines) + "\n")
 
 
-if __name__ == "__main__" and sys.argv[1:2] == ["box"]:
+def _seed_line(args):
+    side, seed = args
+    return run(f"poisson3d_{side}_xstar{seed}", W.poisson3d(side, xstar_seed=seed), 8, 25)
+
+
+def main_seeds(side):
+    import multiprocessing as mp
+    lines = [f"# oracle (FP64, 1 thread per run) to ||r||/||r0|| < 1e-8; 7-point Poisson {side}^3, s = 8, "
+             "nu = 25, Jacobi, bounds gersh_lanczos10 (seed 5000); x* ~ U(-1,1) from the seed in the name",
+             "# written by tests/golden/make_oracle_outer_counts.py seeds"]
+    with mp.get_context("spawn").Pool(len(SPREAD_SEEDS)) as pool:
+        lines += pool.map(_seed_line, [(side, sd) for sd in SPREAD_SEEDS])
+    with open(OUT_SEEDS, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+if __name__ == "__main__" and sys.argv[1:2] == ["seeds"]:
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    main_seeds(int(sys.argv[2]) if len(sys.argv) > 2 else 128)
+elif __name__ == "__main__" and sys.argv[1:2] == ["box"]:
     main_box([int(v) for v in sys.argv[2:]] or [64, 128, 230])
 elif __name__ == "__main__":
     sides = [int(v) for v in sys.argv[1:]] or [64, 128, 256]

@@ -123,3 +123,39 @@ def test_invalid_csr_rejected_on_host(abi):
 def test_status_strings(abi):
     for code, name in abi.STATUS.items():
         assert abi.sstep_cg_status_string(code) == name
+
+
+@pytest.mark.parametrize("bad", [dict(gram_form=3), dict(gram_form=2, block_conjugate=1), dict(refresh_period=0)])
+def test_gram_form_and_refresh_options_checked_on_host(abi, bad):
+    """FUSED (the moments reduced by the step kernels) does not combine with the block
+    conjugation (SSTEP_ERR_UNSUPPORTED); an unknown form or a refresh period below 1 is an
+    invalid argument. All rejected before any CUDA call."""
+    with pytest.raises(abi.SStepError) as ei:
+        abi.sstep_cg_create_stencil(3, 8, 8, 8, None, abi.sstep_cg_default_opts(**bad), stream=0)
+    assert ei.value.status == (7 if bad.get("block_conjugate") else 1)
+    assert abi.sstep_cg_last_error(None)
+
+
+def test_noalloc_arguments_checked_on_host(abi):
+    """sstep_gram_fgs_noalloc validates every argument before its first CUDA call: sizes, the
+    static scratch's limit s <= 16, bounds, the preconditioner and the pointers (the fake
+    device addresses below are never dereferenced)."""
+    lib = abi.lib
+    P, out, md = 4096, 8192, 12288
+    good = dict(n=64, s=4, nu=10, solver=0, P=P, ldp=64, md=None, mc=4.0, lo=0.1, hi=2.0, out=out)
+
+    def call(**kw):
+        a = dict(good, **kw)
+        return lib.sstep_gram_fgs_noalloc(a["n"], a["s"], a["nu"], a["solver"], a["P"], a["ldp"], a["md"], a["mc"],
+                                          a["lo"], a["hi"], a["out"], None)
+
+    for bad in (dict(P=None), dict(out=None), dict(s=0), dict(s=17), dict(n=0), dict(ldp=63), dict(nu=0),
+                dict(nu=10001), dict(solver=2), dict(lo=2.0, hi=2.0), dict(lo=3.0), dict(lo=-0.5),
+                dict(md=None, mc=0.0), dict(md=None, mc=-1.0)):
+        assert call(**bad) == 1, bad
+        msg = lib.sstep_cg_last_error(None).decode()
+        assert msg.startswith("sstep_gram_fgs_noalloc:"), (bad, msg)
+        if bad.get("s") in (0, 17):
+            assert "16" in msg
+    # mdiag given: mconst is not used
+    assert call(md=md, mc=0.0, s=17) == 1

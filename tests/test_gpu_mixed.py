@@ -121,3 +121,54 @@ def test_mixed_conversions_round_to_nearest_even_and_back_exactly():
         ref = (x * 2.0 ** k).float()
         assert torch.equal(out, ref) or bool(torch.all((out == ref) | (torch.isnan(out) & torch.isnan(ref))))
         assert torch.equal(back, out.double())
+
+
+REFRESH_CASES = [
+    ("poisson3d_48_fused", lambda: W.poisson3d(48), 8, 25, "fused"),
+    ("poisson3d_odd_ragged_fused", lambda: W.make("p3", (19, 13, 11), config=12), 8, 25, "fused"),
+    ("diffusion3d_ragged_moments", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), 12, 30, "moments"),
+    ("diffusion2d_direct", lambda: W.make("d2", (45, 33), kappa_sigma=0.5, config=13), 8, 20, "direct"),
+]
+
+
+@pytest.mark.parametrize("name,make,s,nu,form", REFRESH_CASES, ids=[c[0] for c in REFRESH_CASES])
+@pytest.mark.parametrize("period", [1, 2, 3, 4])
+def test_mixed_refresh_period_reaches_fp64_tolerance(name, make, s, nu, form, period):
+    """The mixed form with the FP64 residual refreshed every `period` outer iterations (the
+    others update the FP32 residual recursively and test convergence on it): every form of the
+    Gram reaches the FP64 true relative residual 1e-8, with a solution within 1e-5 of the FP64
+    oracle's and an outer count close to the oracle's; the graph-driven loop equals the host
+    loop bit for bit (period 3 does not divide the host loop's 8 outer iterations per check)."""
+    p = make()
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+    ref = O.solve(op, p.b, s=s, nu=nu, lam_min=lam[0], lam_max=lam[1], tol=1e-8)
+    b = _dev(p.b)
+    kw = dict(bounds=lam, s=s, nu=nu, tol=1e-8, precision="mixed", gram_form=form, refresh_period=period)
+    sv = _solver(p, "stencil", **kw)
+    x, info = sv.solve(b)
+    assert info["status"] == "SSTEP_OK", info
+    xn = x.cpu().numpy()
+    true_rel = np.linalg.norm(p.b - op.matvec(xn)) / np.linalg.norm(p.b)
+    assert true_rel <= 1e-8 and info["rel_res_true"] <= 1e-8
+    err = _rel(xn, ref.x)
+    print(f"{name} period {period}: mixed outers {info['outer_iters']} (refreshes {info['refreshes']}) vs fp64 "
+          f"oracle {ref.outer_iters}; |x_mixed - x_oracle| / |x_oracle| = {err:.3e}")
+    assert err <= 1e-5
+    assert info["outer_iters"] <= int(1.25 * ref.outer_iters) + period + 2
+    sg = _solver(p, "stencil", use_graph=1, **kw)
+    xg, ig = sg.solve(b)
+    assert ig["outer_iters"] == info["outer_iters"] and torch.equal(xg, x)
+
+
+def test_mixed_fused_first_iterate_at_fp32_level():
+    p = W.poisson3d(32)
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+    ref = O.solve(op, p.b, s=8, nu=25, lam_min=lam[0], lam_max=lam[1], tol=1e-30, max_outer=2, history=2)
+    for k in (1, 2):
+        sv = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-30, max_outer=k, precision="mixed",
+                     gram_form="fused", check_every=1, refresh_period=2)
+        x, info = sv.solve(_dev(p.b))
+        assert info["outer_iters"] == k
+        assert _rel(x.cpu().numpy(), ref.history[k - 1].x) <= 1e-5, k

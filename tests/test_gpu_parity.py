@@ -125,11 +125,26 @@ SOLVE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("name,make,mode,s,nu", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
-@pytest.mark.parametrize("form", ["direct", "moments"])
+# cases whose operator admits the fused moments (stencil, constant M): the pair kernel (nx
+# even), the one-point kernel (nx odd), 2D and 3D
+FUSED_CASES = [
+    ("config1_poisson2d_64_stencil", W.poisson2d_64, "stencil", 4, 20),
+    ("poisson3d_32_stencil_s8", lambda: W.poisson3d(32), "stencil", 8, 25),
+    ("poisson3d_even_ragged_s8", lambda: W.make("p3e", (70, 13, 11), config=17), "stencil", 8, 25),
+    ("poisson3d_odd_ragged_s12", lambda: W.make("p3", (19, 13, 11), config=12), "stencil", 12, 30),
+    ("poisson2d_odd_s1", lambda: W.make("p2", (37, 29), config=11), "stencil", 1, 5),
+]
+
+
+@pytest.mark.parametrize("name,make,mode,s,nu", SOLVE_CASES + FUSED_CASES[3:],
+                         ids=[c[0] for c in SOLVE_CASES + FUSED_CASES[3:]])
+@pytest.mark.parametrize("form", ["direct", "moments", "fused"])
 def test_per_iterate_parity_first_five_outer_iterations(name, make, mode, s, nu, form):
     """x_k and r_k, k = 1..5, within 1e-10 of the oracle (which forms G = P^T A P directly)
-    for both ways of forming G on the GPU."""
+    for every way of forming G on the GPU (fused: the moments reduced by the step kernels,
+    where the operator allows it)."""
+    if form == "fused" and name not in [c[0] for c in FUSED_CASES]:
+        pytest.skip("fused moments need a stencil operator with a constant M")
     p = make()
     op = O.Operator(*p.csr())
     lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
@@ -219,7 +234,7 @@ def test_host_buffer_solve_matches_device_solve():
     assert np.array_equal(xh, xd.cpu().numpy())
 
 
-@pytest.mark.parametrize("form", ["direct", "moments"])
+@pytest.mark.parametrize("form", ["direct", "moments", "fused"])
 def test_full_solve_outer_counts_match_stored_oracle_runs(form):
     """64^3, 128^3 and 256^3 Poisson (s = 8, nu = 25) to 1e-8 against the outer-iteration
     counts of the oracle's own converged runs (tests/golden/oracle_outer_counts.txt). The
@@ -248,22 +263,74 @@ def test_full_solve_outer_counts_match_stored_oracle_runs(form):
             (side, info["outer_iters"], stored[side])
 
 
+_REF_256 = {}
+
+
+def _oracle_256():
+    """The oracle's first five iterates at 256^3 (computed once per test session)."""
+    if not _REF_256:
+        p = W.poisson3d(256)
+        op = O.Operator(*p.csr())
+        lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+        ref = O.solve(op, p.b, s=8, nu=25, lam_min=lam[0], lam_max=lam[1], tol=1e-30, max_outer=5, history=5)
+        _REF_256.update(p=p, lam=lam, ref=ref)
+    return _REF_256["p"], _REF_256["lam"], _REF_256["ref"]
+
+
 @pytest.mark.slow
-def test_full_size_poisson3d_256_first_five_iterates():
-    """256^3 (16.8M unknowns), s = 8, nu = 25, stencil operator as the benchmark runs it:
-    every entry of x_k and r_k for k = 1..5 against the oracle."""
-    p = W.poisson3d(256)
-    op = O.Operator(*p.csr())
-    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
-    ref = O.solve(op, p.b, s=8, nu=25, lam_min=lam[0], lam_max=lam[1], tol=1e-30, max_outer=5, history=5)
-    sv = _solver(p, "stencil", s=8, nu=25)
+@pytest.mark.parametrize("form", ["moments", "direct", "fused"])
+def test_full_size_poisson3d_256_first_five_iterates(form):
+    """256^3 (16.8M unknowns), s = 8, nu = 25, stencil operator as the benchmark runs it, with
+    both ways of forming G (moments: the benchmark's headline form): every entry of x_k and
+    r_k for k = 1, 3, 5 against the oracle."""
+    p, lam, ref = _oracle_256()
+    sv = _solver(p, "stencil", s=8, nu=25, gram_form=form)
     lo, hi = sv.bounds
     assert lo == pytest.approx(lam[0], rel=1e-9) and hi == lam[1]
+    sv.close()
     b = _dev(p.b)
     for k in (1, 3, 5):
-        sv2 = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-30, max_outer=k)
+        sv2 = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-30, max_outer=k, gram_form=form)
         x, info = sv2.solve(b)
+        assert info["outer_iters"] == k
         h = ref.history[k - 1]
-        assert _rel(x.cpu().numpy(), h.x) <= 1e-10
-        assert _rel(sv2.residual().cpu().numpy(), h.r) <= 1e-10
+        assert _rel(x.cpu().numpy(), h.x) <= 1e-10, (form, k, _rel(x.cpu().numpy(), h.x))
+        assert _rel(sv2.residual().cpu().numpy(), h.r) <= 1e-10, (form, k)
         sv2.close()
+
+
+def test_fused_form_reaches_tolerance_like_oracle_and_graph_equals_host_loop():
+    """Full solves with the fused moments (FP64) on a 2D and a 3D Poisson problem: true
+    residual <= 1e-8, outer count within one of the oracle's, the solution within 1e-7; the
+    CUDA-graph loop gives the host loop's result bit for bit."""
+    for p, s, nu in ((W.poisson2d_64(), 4, 20), (W.poisson3d(40), 8, 25)):
+        op = O.Operator(*p.csr())
+        lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+        ref = O.solve(op, p.b, s=s, nu=nu, lam_min=lam[0], lam_max=lam[1], tol=1e-8)
+        b = _dev(p.b)
+        sv = _solver(p, "stencil", bounds=lam, s=s, nu=nu, tol=1e-8, gram_form="fused")
+        x, info = sv.solve(b)
+        assert info["status"] == "SSTEP_OK" and info["rel_res_true"] <= 1e-8, info
+        assert abs(info["outer_iters"] - ref.outer_iters) <= 1, (info["outer_iters"], ref.outer_iters)
+        assert _rel(x.cpu().numpy(), ref.x) <= 1e-7
+        sg = _solver(p, "stencil", bounds=lam, s=s, nu=nu, tol=1e-8, gram_form="fused", use_graph=1)
+        xg, ig = sg.solve(b)
+        assert torch.equal(x, xg) and ig["outer_iters"] == info["outer_iters"]
+
+
+def test_fused_form_rejects_operators_without_constant_m():
+    from paper_2512_09642_gb300 import abi
+    p = W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14)
+    for mode in ("stencil", "csr"):
+        with pytest.raises(abi.SStepError) as ex:
+            _solver(p, mode, bounds=(0.04, 2.0), s=4, gram_form="fused")
+        assert ex.value.status == 7   # SSTEP_ERR_UNSUPPORTED
+    # diffusion without a preconditioner has M = I: allowed, and per-iterate equal to the oracle
+    op = O.Operator(*p.csr(), precond="none")
+    lam = (0.1, 8.5 * 9)
+    ref = O.solve(op, p.b, s=4, nu=20, lam_min=lam[0], lam_max=lam[1], tol=1e-30, max_outer=3, history=3)
+    sv = _solver(p, "stencil", bounds=lam, s=4, nu=20, tol=1e-30, max_outer=3, precond="none",
+                 gram_form="fused", check_every=1)
+    x, info = sv.solve(_dev(p.b))
+    assert info["outer_iters"] == 3
+    assert _rel(x.cpu().numpy(), ref.history[2].x) <= 1e-10

@@ -362,6 +362,31 @@ def test_monomial_versus_chebyshev_conditioning():
     assert cl["cheb_kappa_order_at_s10"] / 10 <= k10 <= cl["cheb_kappa_order_at_s10"] * 10
 
 
+def test_monomial_basis_is_the_matrix_powers():
+    """Section 4's contrast basis p_j = (M^-1 A)^j r against explicit dense matrix powers, with
+    a non-constant Jacobi diagonal (so a dropped M^-1 or a misplaced one shows) and with M = I
+    (against the eigendecomposition A^j r = V diag(lambda^j) V^T r)."""
+    p = W.make("mono", (9, 8), kappa_sigma=0.7, config=21)
+    for precond in ("jacobi", "none"):
+        op = O.Operator(*p.csr(), precond=precond)
+        A = _dense(op)
+        d = np.diag(A)
+        assert np.ptp(d) > 0.5   # the diagonal is far from constant
+        B = A / d[:, None] if precond == "jacobi" else A
+        r = rng.uniform(31, op.n)
+        s = 7
+        P = O.monomial_basis(op, r, s)
+        assert P.shape == (op.n, s)
+        for j in range(s):
+            ref = np.linalg.matrix_power(B, j) @ r
+            assert np.linalg.norm(P[:, j] - ref) <= 1e-12 * np.linalg.norm(ref), (precond, j)
+        if precond == "none":
+            lam, V = np.linalg.eigh(A)
+            for j in range(s):
+                ref = V @ (lam ** j * (V.T @ r))
+                assert np.linalg.norm(P[:, j] - ref) <= 1e-11 * np.linalg.norm(ref), j
+
+
 # --- whole solves -----------------------------------------------------------------------
 
 def test_s1_is_steepest_descent():

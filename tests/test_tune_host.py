@@ -59,3 +59,31 @@ def test_prediction_and_choice_follow_the_fitted_model(tune, monkeypatch):
     assert res.best["s"] == best_s and res.predicted_s == pytest.approx(want[best_s], rel=1e-9)
     assert set(res.best) == {"s", "nu", "gram_form", "batch_chunk", "batch_ctas_per_sm"}
     assert len(res.sample) == 8
+
+
+def test_second_stage_picks_the_fastest_launch_shape(tune, monkeypatch):
+    """The shape stage re-solves the sample at the first stage's (s, nu, form) for every launch
+    shape (unknowns per Gram/update item x resident stencil blocks per SM) and keeps the one
+    with the smallest predicted batch time; shapes do not change the outer counts here."""
+    grids = [(s, s) for s in (32, 64, 96, 128, 160, 192, 224, 256)]
+    speed = {(4096, 4): 1.30, (4096, 6): 1.10, (4096, 8): 1.20, (8192, 4): 1.05, (8192, 6): 1.00,
+             (8192, 8): 0.97, (16384, 4): 1.15, (16384, 6): 0.91, (16384, 8): 0.99}
+    calls = []
+
+    def fake_solve(sg, sk, sb, cand, tol, max_outer, stream=None):
+        calls.append(dict(cand))
+        n = np.array([g[0] * g[1] for g in sg], dtype=np.float64)
+        N = (2.0 if cand["s"] == 8 else 3.0) * n ** 0.5
+        c = 1e-6 * speed[(cand["batch_chunk"], cand["batch_ctas_per_sm"])]
+        return c * float(np.sum(n * N)), list(N), ["SSTEP_OK"] * len(sg)
+
+    monkeypatch.setattr(tune, "_solve_sample", fake_solve)
+    cands = [{"s": s, "nu": 20, "gram_form": "moments", "batch_chunk": 8192, "batch_ctas_per_sm": 6} for s in (6, 8)]
+    res = tune.tune(grids, [None] * len(grids), [None] * len(grids), candidates=cands, sample=6)
+    assert res.best == {"s": 8, "nu": 20, "gram_form": "moments", "batch_chunk": 16384, "batch_ctas_per_sm": 6}
+    shape_rows = [r for r in res.table if r["stage"] == "shape"]
+    assert len(shape_rows) == 8 and all(r["s"] == 8 for r in shape_rows)   # 9 shapes, one already measured
+    assert len(calls) == 2 + 8
+    # without the second stage the first stage's choice stands
+    res1 = tune.tune(grids, [None] * len(grids), [None] * len(grids), candidates=cands, sample=6, shapes=[])
+    assert res1.best["batch_chunk"] == 8192 and res1.best["batch_ctas_per_sm"] == 6

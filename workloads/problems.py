@@ -256,9 +256,10 @@ def poisson2d_64() -> Problem:
     return make("poisson2d_64", (64, 64), config=1, s=4, nu=20)
 
 
-def poisson3d(side: int = 256, s: int = 8, nu: int = 25) -> Problem:
-    """3D 7-point Poisson side**3 (256**3 = 16.8M unknowns), s = 8, nu = 25."""
-    return make(f"poisson3d_{side}", (side, side, side), config=2, s=s, nu=nu)
+def poisson3d(side: int = 256, s: int = 8, nu: int = 25, xstar_seed: Optional[int] = None) -> Problem:
+    """3D 7-point Poisson side**3 (256**3 = 16.8M unknowns), s = 8, nu = 25; x* from seed
+    1002 unless xstar_seed is given."""
+    return make(f"poisson3d_{side}", (side, side, side), config=2, s=s, nu=nu, xstar_seed=xstar_seed)
 
 
 def diffusion3d(side: int = 384, s: int = 12, nu: int = 30, sigma: float = 1.0) -> Problem:
