@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-plain-loop", action="store_true")
     ap.add_argument("--cpu-outers", type=int, default=2)
+    ap.add_argument("--no-spread", action="store_true",
+                    help="poisson3d: skip the headline form's solves of four more seeded x*")
     ap.add_argument("--csr", action="store_true",
                     help="poisson3d: give the operator as a CSR matrix (int32 indices, FP64 values) instead of the "
                          "matrix-free stencil")
@@ -186,10 +188,11 @@ def measured_traffic(workload, form, logical):
     return None
 
 
-# FP64 pipe rate derived from the nominal 1.25 TFLOP/s FP64 of GB300 (152 SMs, 2070 MHz):
-# 1.25e12 / 2 flops per FMA = 0.625e12 FP64 instructions per second (152 x 2.06 per clock x
-# 2.07 GHz); an FP64 add, multiply or FMA each occupies one of them.
-FP64_OPS_PEAK = 0.625e12
+# FP64 issue rate measured on GB300 (profiles/fp64_issue_rate_gb300.md): FMAs at 627.9 G
+# lane-operations/s (2 per SM per clock at 2070 MHz, 152 SMs); adds and multiplies issue at
+# only 528 G, which is why the FP64 stencils write their additions as FMAs.
+FP64_OPS_PEAK = 0.6279e12
+FP64_PEAK_KIND = "measured: FP64 FMA issue rate, 627.9 G lane-ops/s at 2070 MHz (profiles/fp64_issue_rate_gb300.md)"
 
 
 def form_gram(form):
@@ -444,7 +447,7 @@ def run_reference(args):
     }))
 
 
-def measure_form(args, p, b, world, local, precision, csr=None, fixed_outers=None):
+def measure_form(args, p, b, world, local, precision, csr=None, fixed_outers=None, e2e=True):
     """Warm-up + K timed solves of one form; per-kernel durations from the sampled events.
     fixed_outers: run exactly that many outer iterations per solve (tol 1e-30), sampling the
     kernels in every chunk of 8, and skip the end-to-end leg."""
@@ -492,7 +495,7 @@ def measure_form(args, p, b, world, local, precision, csr=None, fixed_outers=Non
     t_solve = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3, world)
 
     t_e2e = None
-    if not args.no_e2e and not fixed_outers:
+    if e2e and not args.no_e2e and not fixed_outers:
         # end to end through the C ABI with pinned host buffers, copies inside the timed region
         bh = torch.as_tensor(p.b).pin_memory()
         xh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -546,7 +549,7 @@ def kernel_report(args, n, infos, precision, dim=3, diffusion=False, box=False, 
     hbm_frac = by / d / 1e9 / hbm_peak
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": ops / d / 1e9, "peak": FP64_OPS_PEAK / 1e9, "unit": "G FP64-op/s",
-                "frac": alu_frac, "peak_kind": "derived: nominal 1.25 TFLOP/s FP64 = 152 SMs x 2 FP64 FMA/clk x 2.07 GHz"}
+                "frac": alu_frac, "peak_kind": FP64_PEAK_KIND}
     else:
         roof = {"bound": "hbm", "achieved": by / d / 1e9, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
@@ -595,7 +598,8 @@ def run_ours(args):
     forms = {}
     res = {}
     for prec in args.forms.split(","):
-        r = measure_form(args, p, b, world, local, prec, csr)
+        # the end-to-end leg (host buffers, copies timed) for the headline form only
+        r = measure_form(args, p, b, world, local, prec, csr, e2e=prec == args.forms.split(",")[0])
         dim = len(p.dims)
         diff = p.kappa is not None
         # (graph runs report times only: no kernel sampling inside a graph)
@@ -635,6 +639,29 @@ def run_ours(args):
         if tr:
             h["roofline"]["traffic"] = tr["bytes"]
             h["roofline"]["traffic_source"] = f"ncu capture of {tr['kernel']}, profiles/{tr['profile']}"
+
+    spread = None
+    if args.workload == "poisson3d" and csr is None and not args.no_spread and not args.graph:
+        # the headline form on the five seeded x* (the first is the workload's): the outer
+        # count to 1e-8 of this restarted iteration moves with rounding, the time per outer
+        # iteration does not
+        from paper_2512_09642_gb300 import SStepCG, abi
+        parts = head.split("+")
+        sv = SStepCG(grid=p.dims, s=s, nu=nu, tol=1e-8, check_every=8, precision=parts[0], gram_form=form_gram(head),
+                     block_conjugate=1 if "conj" in parts else 0,
+                     refresh_period=form_refresh(head) if parts[0] == "mixed" else 1)
+        runs = []
+        for sd in SPREAD_SEEDS:
+            bq = b if sd == SPREAD_SEEDS[0] else torch.as_tensor(W.poisson3d(side, xstar_seed=sd).b).cuda()
+            xq = torch.zeros(n, dtype=torch.float64, device="cuda")
+            inf = abi.sstep_cg_solve(sv.h, bq, xq).as_dict()
+            runs.append({"xstar_seed": sd, "outer_iters": inf["outer_iters"], "time_s": inf["ms"] / 1e3,
+                         "ms_per_outer": inf["ms"] / max(inf["outer_iters"], 1), "rel_res_true": inf["rel_res_true"]})
+        sv.close()
+        cnt = sorted(r["outer_iters"] for r in runs)
+        tms = sorted(r["time_s"] for r in runs)
+        spread = {"form": head, "outer_min": cnt[0], "outer_median": cnt[2], "outer_max": cnt[-1],
+                  "time_median_s": tms[2], "runs": runs}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("poisson3d", "poisson27"):
@@ -687,7 +714,8 @@ def run_ours(args):
             "outer_iters": h["outer_iters"], "rel_res_true": h["rel_res_true"], "outer_per_s": h["outer_per_s"],
             "hbm_gbs_model": h["hbm_gbs_model"], "roofline": h["roofline"],
             "e2e": {"value": h["e2e_s"], "unit": "s", "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
-            "gpu_launches": h["gpu_launches"], "clocks": h["clocks"], "cpu_baseline": cpu, "forms": forms,
+            "gpu_launches": h["gpu_launches"], "clocks": h["clocks"], "cpu_baseline": cpu,
+            "ms_per_outer": h["ms_per_outer"], "xstar_spread": spread, "forms": forms,
         }
         print(json.dumps(line))
 
@@ -949,7 +977,7 @@ def run_spread(args):
 
 
 def parse_default_forms():
-    return "fp64+mom,mixed+mom,fp64,mixed,fp64+mom+conj"
+    return "fp64+mom,mixed+fused+r4,fp64,fp64+fused,mixed+mom,mixed+fused,fp64+mom+conj"
 
 
 def main():

@@ -736,8 +736,9 @@ __global__ void __launch_bounds__(FIN_THREADS) k_moments_finish(const T* __restr
         const T* base = part + (size_t)(2 * j + q) * NC * nblk;
         double acc = 0.0;
         for (int b = lo + lane; b < hi; b += 32) {
-            double x = (double)base[b];
-            if (NC == 2) x += (double)base[nblk + b];
+            double x;
+            if constexpr (NC == 2) x = f2d_exact(__ldg(base + b)) + f2d_exact(__ldg(base + nblk + b));
+            else x = __ldg(base + b);
             acc += x;
         }
         acc = warp_sum(acc);

@@ -33,10 +33,13 @@ template <typename T> __device__ __forceinline__ T add1(T a, T b, T one) { retur
 // Fused moments (gram_form FUSED): the step that writes p_(j+1) also reduces a_j = <p_j, p_j>
 // and b_j = <p_j, p_(j+1)> (unweighted; M is a constant multiple of I), from which the Gram
 // finish forms every Chebyshev moment, so no pass re-reads the basis. Per-thread sums in the
-// step's precision (FP32: exact products summed as compensated pairs, Dot2), then a fixed
+// step's precision over the thread's 16 (pair kernel; 8 or 16 otherwise) points, then a fixed
 // warp butterfly and a fixed order over the block's warps; one partial per block and value:
-// FP64 double[2][nblk] (a, b), FP32 float[4][nblk] (a_hi, a_lo, b_hi, b_lo). The FP32 form
-// adds no FP64 instruction to the step.
+// FP64 double[2][nblk] (a, b), FP32 float[4][nblk] (a_hi, a_lo, b_hi, b_lo). In FP32 the
+// per-thread sums are plain FMAs (their rounding is independent from thread to thread, so
+// the million per-thread errors of about 1e-7 average out in the FP64 total) and everything
+// from the warp butterfly on is exact pair arithmetic (TwoSum on the high parts); the FP32
+// form adds no FP64 instruction to the step.
 template <typename T> struct MomAcc;
 template <> struct MomAcc<double> {
     double a = 0.0, b = 0.0;
@@ -48,8 +51,8 @@ template <> struct MomAcc<double> {
 template <> struct MomAcc<float> {
     float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
     __device__ __forceinline__ void add(float pj, float pn) {
-        dot2_acc(pj, pj, ah, al);
-        dot2_acc(pj, pn, bh, bl);
+        ah = fmaf(pj, pj, ah);
+        bh = fmaf(pj, pn, bh);
     }
 };
 
@@ -260,70 +263,26 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_poisson_pair(const T* __restric
     if (GRAM) mom_block_store(acc, mom, nblk);
 }
 
-// CSR rows, one per thread, in tiles of RB consecutive rows per block. The tile's nonzeros
-// (values and column indices, contiguous in memory) are first copied to shared memory with
-// coalesced loads - each warp request then covers whole cache lines, where a thread walking
-// its own row would make 32 requests scattered over the warp's rows - and every thread forms
-// its row's dot product from there, in the row's order (the FMA sequence of a plain row loop,
-// so the result is the same bit for bit). A tile with more than CSR_CAP nonzeros (rows much
-// longer than a stencil's) reads them from global memory instead.
-constexpr int CSR_CAP = 9 * RB;
-
-template <typename T> struct CsrTile {
-    T v[CSR_CAP];
-    int32_t c[CSR_CAP];
-};
-
-// (A p)_row for row = row0 + threadIdx.x (0 past the end). Called by every thread of the block
-// with the same row0; contains two block barriers.
-template <typename T>
-__device__ __forceinline__ T csr_tile_dot(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                                          const T* __restrict__ vals, const T* __restrict__ p, int64_t n, int64_t row0,
-                                          CsrTile<T>& tile) {
-    const int t = threadIdx.x;
-    const int64_t row = row0 + t;
-    const int64_t rend = row0 + RB < n ? row0 + RB : n;
-    const int32_t b0 = ldg(rowptr + row0);
-    const int cnt = ldg(rowptr + rend) - b0;
-    const bool staged = cnt <= CSR_CAP;   // the same for the whole block
-    if (staged) {
-#pragma unroll 4
-        for (int k = t; k < cnt; k += RB) {
-            tile.v[k] = ldg(vals + b0 + k);
-            tile.c[k] = ldg(colind + b0 + k);
-        }
-    }
-    __syncthreads();
-    T y = T(0);
-    if (row < n) {
-        const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
-        if (staged) {
-            for (int k = s0 - b0; k < s1 - b0; ++k) y = fma(tile.v[k], ldg(p + tile.c[k]), y);
-        } else {
-            for (int32_t k = s0; k < s1; ++k) y = fma(ldg(vals + k), ldg(p + ldg(colind + k)), y);
-        }
-    }
-    __syncthreads();   // the next tile overwrites the shared copy
-    return y;
-}
-
-// CSR Chebyshev step: y = A p, out = cdv (y) - c sigma p - q.
+// CSR Chebyshev step, one thread per row: y = A p, out = cdv (y) - c sigma p - q. A warp's
+// loads of vals / colind are strided by the row length, but the warp's rows share their
+// cache lines, which L1 keeps between the row's iterations: measured at 0.95 (FP64) and 0.93
+// (FP32) of the HBM rate for the 7-point matrix at 256^3. Staging each 256-row tile's entries
+// in shared memory with coalesced loads first was measured 1.6x slower (its barriers expose
+// the load latency).
 template <typename T, bool FIRST, bool JACOBI>
 __global__ void __launch_bounds__(RB) k_cheb_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                                                  const T* __restrict__ vals, const T* __restrict__ cdinv,
                                                  const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ out,
                                                  int64_t n, T c, T csig, T cscale, const Ctl* __restrict__ ctl) {
     if (ctl->done) return;
-    __shared__ CsrTile<T> tile;
-    for (int64_t row0 = blockIdx.x * (int64_t)RB; row0 < n; row0 += (int64_t)gridDim.x * RB) {
-        const T y = csr_tile_dot<T>(rowptr, colind, vals, p, n, row0, tile);
-        const int64_t r = row0 + threadIdx.x;
-        if (r < n) {
-            T cdv = JACOBI ? ldg(cdinv + r) : c;
-            if (FIRST && JACOBI) cdv *= cscale;
-            const T pc = ldg(p + r);
-            out[r] = FIRST ? fma(cdv, y, -csig * pc) : fma(cdv, y, fma(-csig, pc, -ldg(q + r)));
-        }
+    for (int64_t r = blockIdx.x * (int64_t)RB + threadIdx.x; r < n; r += (int64_t)gridDim.x * RB) {
+        const int32_t b = ldg(rowptr + r), en = ldg(rowptr + r + 1);
+        T y = T(0);
+        for (int32_t t = b; t < en; ++t) y = fma(ldg(vals + t), ldg(p + ldg(colind + t)), y);
+        T cdv = JACOBI ? ldg(cdinv + r) : c;
+        if (FIRST && JACOBI) cdv *= cscale;
+        const T pc = ldg(p + r);
+        out[r] = FIRST ? fma(cdv, y, -csig * pc) : fma(cdv, y, fma(-csig, pc, -ldg(q + r)));
     }
 }
 
@@ -474,16 +433,14 @@ __global__ void __launch_bounds__(RB) k_residual_csr(const int32_t* __restrict__
         kscale -= 1;
     }
     double ss = 0.0;
-    __shared__ CsrTile<double> tile;
-    for (int64_t row0 = blockIdx.x * (int64_t)RB; row0 < n; row0 += (int64_t)gridDim.x * RB) {
-        const double y = csr_tile_dot<double>(rowptr, colind, vals, x, n, row0, tile);
-        const int64_t row = row0 + threadIdx.x;
-        if (row < n) {
-            const double rv = ldg(b + row) - y;
-            if (r) r[row] = rv;
-            if (r32) r32[row] = d2f_scaled(rv, kscale);
-            ss = fma(rv, rv, ss);
-        }
+    for (int64_t row = blockIdx.x * (int64_t)RB + threadIdx.x; row < n; row += (int64_t)gridDim.x * RB) {
+        const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
+        double y = 0.0;
+        for (int32_t t = s0; t < s1; ++t) y = fma(ldg(vals + t), ldg(x + ldg(colind + t)), y);
+        const double rv = ldg(b + row) - y;
+        if (r) r[row] = rv;
+        if (r32) r32[row] = d2f_scaled(rv, kscale);
+        ss = fma(rv, rv, ss);
     }
     __shared__ double sh[RB / 32];
     const double tot = block_sum<RB>(ss, sh);
@@ -744,10 +701,11 @@ dim3 box_grid(const OpDesc& op) {
 __global__ void __launch_bounds__(RB) k_apply_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                                                   const double* __restrict__ vals, const double* __restrict__ x,
                                                   double* __restrict__ y, int64_t n) {
-    __shared__ CsrTile<double> tile;
-    for (int64_t row0 = blockIdx.x * (int64_t)RB; row0 < n; row0 += (int64_t)gridDim.x * RB) {
-        const double acc = csr_tile_dot<double>(rowptr, colind, vals, x, n, row0, tile);
-        if (row0 + threadIdx.x < n) y[row0 + threadIdx.x] = acc;
+    for (int64_t row = blockIdx.x * (int64_t)RB + threadIdx.x; row < n; row += (int64_t)gridDim.x * RB) {
+        const int32_t s0 = ldg(rowptr + row), s1 = ldg(rowptr + row + 1);
+        double acc = 0.0;
+        for (int32_t t = s0; t < s1; ++t) acc = fma(ldg(vals + t), ldg(x + ldg(colind + t)), acc);
+        y[row] = acc;
     }
 }
 

@@ -58,10 +58,49 @@ __global__ void __launch_bounds__(UB) k_update_mixed(float* __restrict__ P, int6
     __syncthreads();
     const double inv_scale = 1.0 / ctl->scale;   // exact: scale is a power of two
     constexpr int NC = WR ? S + 1 : S;
-    for (int64_t e = blockIdx.x * (int64_t)UB + threadIdx.x; e < n; e += (int64_t)gridDim.x * UB) {
+    // two consecutive unknowns per thread and iteration: 8-byte loads of the FP32 columns (ld
+    // is even, the columns 8-byte aligned) and 16-byte loads and stores of x (16-byte aligned),
+    // half the load instructions of one unknown at a time; an odd last unknown alone
+    const int64_t npair = n / 2;
+    for (int64_t e2 = blockIdx.x * (int64_t)UB + threadIdx.x; e2 < npair; e2 += (int64_t)gridDim.x * UB) {
+        const int64_t e = 2 * e2;
+        float2 pv[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) pv[j] = __ldg(reinterpret_cast<const float2*>(P + j * ld + e));
+        float sx0 = 0.f, sx1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            sx0 = fmaf(af[j], pv[j].x, sx0);
+            sx1 = fmaf(af[j], pv[j].y, sx1);
+        }
+        double2 xv = *reinterpret_cast<const double2*>(x + e);
+        xv.x = fma(f2d_exact(sx0), inv_scale, xv.x);
+        xv.y = fma(f2d_exact(sx1), inv_scale, xv.y);
+        *reinterpret_cast<double2*>(x + e) = xv;
+        if (WR) {
+            float sr0 = 0.f, sr1 = 0.f;
+#pragma unroll
+            for (int k = 0; k <= S; ++k) {
+                sr0 = fmaf(gf[k], pv[k].x, sr0);
+                sr1 = fmaf(gf[k], pv[k].y, sr1);
+            }
+            float2 rv;
+            if (DV) {
+                const float2 d = __ldg(reinterpret_cast<const float2*>(diag + e));
+                rv.x = fmaf(-d.x, sr0, pv[0].x);
+                rv.y = fmaf(-d.y, sr1, pv[0].y);
+            } else {
+                rv.x = sr0;
+                rv.y = sr1;
+            }
+            *reinterpret_cast<float2*>(P + e) = rv;
+        }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t e = n - 1;
         float pv[NC];
 #pragma unroll
-        for (int j = 0; j < NC; ++j) pv[j] = __ldg(P + j * ld + e);   // all loads in flight first
+        for (int j = 0; j < NC; ++j) pv[j] = P[j * ld + e];
         float sx = 0.f;
 #pragma unroll
         for (int j = 0; j < S; ++j) sx = fmaf(af[j], pv[j], sx);
@@ -70,7 +109,7 @@ __global__ void __launch_bounds__(UB) k_update_mixed(float* __restrict__ P, int6
             float sr = 0.f;
 #pragma unroll
             for (int k = 0; k <= S; ++k) sr = fmaf(gf[k], pv[k], sr);
-            P[e] = DV ? fmaf(-__ldg(diag + e), sr, pv[0]) : sr;
+            P[e] = DV ? fmaf(-diag[e], sr, pv[0]) : sr;
         }
     }
 }
@@ -97,7 +136,10 @@ cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const Ctl* ctl, 
 
 cudaError_t launch_update_mixed(float* P, int64_t ld, int s, int64_t n, double* x, const Ctl* ctl, cudaStream_t st,
                                 bool write_r, const float* diag) {
-    const int nb = blocks_for(n, 8);
+    // the paired loads need 8-byte aligned FP32 columns and diagonal and a 16-byte aligned x
+    if ((ld & 1) || ((uintptr_t)P & 7u) || ((uintptr_t)x & 15u) || (diag && ((uintptr_t)diag & 7u)))
+        return cudaErrorMisalignedAddress;
+    const int nb = blocks_for((n + 1) / 2, 8);
     switch (s) {
 #define SSTEP_CASE(S)                                                                                  \
     case S:                                                                                            \
