@@ -593,9 +593,11 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_box(const T* __restrict__ p, co
 
 // FP32 box step (mixed form): the FP32 pipe has room for the plain 3 x 3 in-plane sums (9
 // loads through L1 and 8 adds per point and plane, the z-window of plane sums in registers),
-// which needs no shared memory and no barriers, so the kernel can run at the HBM rate.
+// which needs no shared memory and no barriers. Its nine loads per point and plane make it
+// latency-bound: eight resident blocks per SM (at most 32 registers) keep enough loads in
+// flight, also with the fused moments' accumulators.
 template <int DIM, bool FIRST, bool GRAM>
-__global__ void __launch_bounds__(BX* BY) k_cheb_box_f32(const float* __restrict__ p, const float* __restrict__ q,
+__global__ void __launch_bounds__(BX* BY, 8) k_cheb_box_f32(const float* __restrict__ p, const float* __restrict__ q,
                                                          float* __restrict__ out, int nx, int ny, int nz, float ca,
                                                          float cb, const Ctl* __restrict__ ctl, void* mom, int nblk) {
     if (ctl->done) return;
