@@ -420,7 +420,7 @@ sstep_status finish_create(sstep_cg_t h) {
                        "box stencil, or precond NONE)");
             return SSTEP_ERR_UNSUPPORTED;
         }
-        h->mom_nblk = cheb_step_blocks(h->op);
+        h->mom_nblk = cheb_step_blocks(h->op, h->mixed);
         CK(cudaMalloc(&h->mom_part, (size_t)16 * h->mom_nblk * h->opts.s));
         CK(cudaMalloc(&h->mom_part2, sizeof(double) * MAX_FIN_BLOCKS * 2 * h->opts.s));
     }

@@ -20,6 +20,12 @@ namespace sstep {
 namespace {
 
 constexpr int BX = 32, BY = 8, KC = 8;      // stencil block (x, y) and z planes per block
+// z planes per block of the 5/7-point and diffusion kernels by precision: 8 for the FP64
+// steps, 16 for the FP32 steps and the FP64 residual (measured at 256^3: the FP32 step 42.6 ->
+// 40.8 us, the mixed refresh 0.284 -> 0.268 ms with 16; the FP64 step 0.233 -> 0.242 ms with
+// 16, 0.233 with 4); KC for the rest
+template <typename T> constexpr int kz_step() { return sizeof(T) == 4 ? 16 : 8; }
+constexpr int KZ_RES = 16;
 constexpr int RB = 256;                      // CSR / vector kernels: threads per block
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
@@ -33,7 +39,8 @@ template <typename T> __device__ __forceinline__ T add1(T a, T b, T one) { retur
 // Fused moments (gram_form FUSED): the step that writes p_(j+1) also reduces a_j = <p_j, p_j>
 // and b_j = <p_j, p_(j+1)> (unweighted; M is a constant multiple of I), from which the Gram
 // finish forms every Chebyshev moment, so no pass re-reads the basis. Per-thread sums in the
-// step's precision over the thread's 16 (pair kernel; 8 or 16 otherwise) points, then a fixed
+// step's precision over the thread's points (2 per plane for the pair kernel, over 8 planes
+// in FP64 and 16 in FP32; 8 or 16 otherwise), then a fixed
 // warp butterfly and a fixed order over the block's warps; one partial per block and value:
 // FP64 double[2][nblk] (a, b), FP32 float[4][nblk] (a_hi, a_lo, b_hi, b_lo). In FP32 the
 // per-thread sums are plain FMAs (their rounding is independent from thread to thread, so
@@ -150,7 +157,7 @@ __device__ __forceinline__ T diffusion_offdiag_sum(const T* __restrict__ p, cons
 // constants folded on the host. Diffusion: out = c1 p - cdv_e s - q (Jacobi, cdv_e = c /
 // diag_e) or out = c ((diag_e - sigma) p - s) - q (no preconditioner). GRAM: also the fused
 // moments a_j, b_j of this block (mom: this step's partials, nblk blocks in the grid).
-template <typename T, int DIM, bool POISSON, bool JACOBI, bool FIRST, bool GRAM>
+template <typename T, int DIM, bool POISSON, bool JACOBI, bool FIRST, bool GRAM, int KZ = kz_step<T>()>
 __global__ void __launch_bounds__(BX* BY) k_cheb_stencil(const T* __restrict__ p, const T* __restrict__ q,
                                                          T* __restrict__ out, int nx, int ny, int nz, Faces<T> f,
                                                          T c1, T c2, T csig, T cscale, const Ctl* __restrict__ ctl,
@@ -161,8 +168,8 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_stencil(const T* __restrict__ p
     MomAcc<T> acc;
     if (i < nx && j < ny) {
         const int64_t sxy = (int64_t)nx * ny;
-        const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
-        const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+        const int k0 = (DIM == 3) ? blockIdx.z * KZ : 0;
+        const int k1 = (DIM == 3) ? min(nz, k0 + KZ) : 1;
         int64_t e = i + (int64_t)nx * j + sxy * k0;
         T pdn = (DIM == 3 && k0 > 0) ? ldg(p + e - sxy) : T(0);
         T pc = ldg(p + e);
@@ -209,7 +216,7 @@ template <typename T> struct Pair;
 template <> struct Pair<double> { using type = double2; };
 template <> struct Pair<float> { using type = float2; };
 
-template <typename T, int DIM, bool FIRST, bool GRAM>
+template <typename T, int DIM, bool FIRST, bool GRAM, int KZ = kz_step<T>()>
 __global__ void __launch_bounds__(BX* BY) k_cheb_poisson_pair(const T* __restrict__ p, const T* __restrict__ q,
                                                               T* __restrict__ out, int nx, int ny, int nz, T c1, T c2,
                                                               const Ctl* __restrict__ ctl, T one, void* mom, int nblk) {
@@ -221,8 +228,8 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_poisson_pair(const T* __restric
     const int j = blockIdx.y * BY + threadIdx.y;
     const bool in = i < nx && j < ny;   // nx even: i + 1 < nx as well
     const int64_t sxy = (int64_t)nx * ny;
-    const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
-    const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+    const int k0 = (DIM == 3) ? blockIdx.z * KZ : 0;
+    const int k1 = (DIM == 3) ? min(nz, k0 + KZ) : 1;
     const int64_t ij = in ? i + (int64_t)nx * j : 0;
     const V zero{T(0), T(0)};
     auto ld2 = [&](int64_t e) { return __ldg(reinterpret_cast<const V*>(p + e)); };
@@ -361,7 +368,7 @@ __device__ void last_block_finish(double mine, double* partials, unsigned int* c
 }
 
 // r = b - A x (FP64) on the stencil, with ||r||^2.
-template <int DIM, bool POISSON>
+template <int DIM, bool POISSON, int KZ = KZ_RES>
 __global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __restrict__ b, const double* __restrict__ x,
                                                              double* __restrict__ r, float* __restrict__ r32, int nx,
                                                              int ny, int nz, Faces<double> f, double d2,
@@ -378,8 +385,8 @@ __global__ void __launch_bounds__(BX* BY) k_residual_stencil(const double* __res
     double ss = 0.0;
     if (act) {
         const int64_t sxy = (int64_t)nx * ny;
-        const int k0 = (DIM == 3) ? blockIdx.z * KC : 0;
-        const int k1 = (DIM == 3) ? min(nz, k0 + KC) : 1;
+        const int k0 = (DIM == 3) ? blockIdx.z * KZ : 0;
+        const int k1 = (DIM == 3) ? min(nz, k0 + KZ) : 1;
         int64_t e = i + (int64_t)nx * j + sxy * k0;
         double pdn = (DIM == 3 && k0 > 0) ? ldg(x + e - sxy) : 0.0;
         double pc = ldg(x + e);
@@ -711,13 +718,13 @@ __global__ void __launch_bounds__(RB) k_apply_csr(const int32_t* __restrict__ ro
     }
 }
 
-dim3 stencil_grid(const OpDesc& op) {
-    return dim3((op.nx + BX - 1) / BX, (op.ny + BY - 1) / BY, op.dim == 3 ? (op.nz + KC - 1) / KC : 1);
+dim3 stencil_grid(const OpDesc& op, int kz = KC) {
+    return dim3((op.nx + BX - 1) / BX, (op.ny + BY - 1) / BY, op.dim == 3 ? (op.nz + kz - 1) / kz : 1);
 }
 
 // two x-adjacent points per thread
-dim3 pair_grid(const OpDesc& op) {
-    const dim3 g = stencil_grid(op);
+dim3 pair_grid(const OpDesc& op, int kz) {
+    const dim3 g = stencil_grid(op, kz);
     return dim3((op.nx + 2 * BX - 1) / (2 * BX), g.y, g.z);
 }
 
@@ -759,7 +766,7 @@ bool use_pair(const OpDesc& op, const T* p, const T* q, const T* out) {
 template <typename T, int DIM, bool POISSON>
 void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, double theta, double sigma, bool first,
                            bool jacobi, const Ctl* ctl, void* mom, cudaStream_t st) {
-    const dim3 grid = stencil_grid(op), block(BX, BY);
+    const dim3 grid = stencil_grid(op, kz_step<T>()), block(BX, BY);
     const double c = first ? theta : 2.0 * theta;
     const Faces<T> f = faces_of<T>(op);
     if (POISSON) {
@@ -769,7 +776,7 @@ void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, dou
         const T c1 = (T)(jacobi ? c * (1.0 - sigma) : c * (d2 - sigma));
         const T c2 = (T)(jacobi ? -c / d2 : -c);
         if (use_pair(op, p, q, out)) {
-            const dim3 g2 = pair_grid(op);
+            const dim3 g2 = pair_grid(op, kz_step<T>());
 #define ARGS p, q, out, op.nx, op.ny, op.nz, c1, c2, ctl, T(1)
             SSTEP_STEP_LAUNCH(k_cheb_poisson_pair, g2, T, DIM);
 #undef ARGS
@@ -796,12 +803,13 @@ void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, dou
 
 }  // namespace
 
-int cheb_step_blocks(const OpDesc& op) {
+int cheb_step_blocks(const OpDesc& op, bool fp32) {
     if (op.kind != OP_STENCIL) return 0;
+    const int kz = fp32 ? kz_step<float>() : kz_step<double>();
     dim3 g;
     if (op.box) g = box_grid(op);
-    else if (op.wx == nullptr && op.nx % 2 == 0) g = pair_grid(op);
-    else g = stencil_grid(op);
+    else if (op.wx == nullptr && op.nx % 2 == 0) g = pair_grid(op, kz);
+    else g = stencil_grid(op, kz);
     return (int)(g.x * g.y * g.z);
 }
 
@@ -875,7 +883,7 @@ size_t residual_partials_needed(const OpDesc& op) {
         return (size_t)g.x * g.y * g.z;
     }
     if (op.kind == OP_STENCIL) {
-        const dim3 g = stencil_grid(op);
+        const dim3 g = stencil_grid(op, KZ_RES);
         return (size_t)g.x * g.y * g.z;
     }
     return (size_t)vec_blocks(op.n);
@@ -890,7 +898,7 @@ cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, 
         return cudaGetLastError();
     }
     if (op.kind == OP_STENCIL) {
-        const dim3 grid = stencil_grid(op), block(BX, BY);
+        const dim3 grid = stencil_grid(op, KZ_RES), block(BX, BY);
         const Faces<double> f = faces_of<double>(op);
         const double d2 = 2.0 * op.dim;
         const bool poisson = op.wx == nullptr;

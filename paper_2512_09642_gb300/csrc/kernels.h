@@ -37,13 +37,13 @@ enum { OP_CSR = 0, OP_STENCIL = 1 };
 // Precision T = double (FP64) or float (mixed form basis). mom != null (stencil operators
 // only): the step also writes its per-block partials of <p, p> and <p, out> there (the fused
 // moments of gram_form FUSED; FP64 double[2][nblk], FP32 float[4][nblk] with nblk =
-// cheb_step_blocks(op)).
+// cheb_step_blocks(op, fp32)).
 template <typename T>
 cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, double theta,
                              double sigma, bool first, bool jacobi, const Ctl* ctl, cudaStream_t st,
                              void* mom = nullptr);
-// Blocks of the stencil step kernel launch_cheb_step uses for op (0 for CSR).
-int cheb_step_blocks(const OpDesc& op);
+// Blocks of the stencil step kernel launch_cheb_step uses for op in FP32 or FP64 (0 for CSR).
+int cheb_step_blocks(const OpDesc& op, bool fp32);
 
 // r = b - A x in FP64; writes r (double, if non-null) and, if r32 != null, the FP32 copy
 // scaled by ctl->scale_next (mode 2); reduces ||r||^2 through `partials` (one double per
