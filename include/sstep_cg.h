@@ -106,6 +106,10 @@ typedef struct {
                               with the same scaled FGS as alpha. FP64, s <= 16 (else
                               SSTEP_ERR_UNSUPPORTED); 2s more basis-length vectors of workspace.
                               0 (default): the restarted iteration of Section 2 as written */
+    int history;           /* > 0: keep a record of the last `history` outer iterations on the
+                              device (sstep_cg_history): the relative residual entering it, the
+                              Gram solve's inexactness delta_k (Section 7) and the smallest
+                              unscaled G_ii; 0 (default): none */
 } sstep_cg_opts;
 
 typedef struct {
@@ -182,6 +186,16 @@ SSTEP_API sstep_status sstep_cg_solve_host(sstep_cg_t handle, const double* b_h,
  * SSTEP_ERR_INVALID_ARG for a CSR or Poisson handle. */
 SSTEP_API sstep_status sstep_cg_grad_kappa(sstep_cg_t handle, const double* x_d, const double* lambda_d,
                                            double* gkappa_d);
+
+/* Per-outer-iteration record of the last solve, oldest first (opts.history > 0): out_h (host,
+ * double[4 * capacity]) receives up to `capacity` records of 4 values each: the outer
+ * iteration's number (1-based), ||r_(k-1)||^2 / ||r_0||^2 of the residual it started from (the
+ * recursive residual; the mixed form's FP64 refresh where one ran), the inexactness
+ * delta_k = ||c~ - G~ a|| / ||c~|| of its Gram solve (Section 7's inexact s-step CG) and its
+ * smallest Gram diagonal G_ii before scaling. *count = the number of records written (at most
+ * min(outer iterations, opts.history, capacity)). SSTEP_ERR_INVALID_ARG when the handle keeps
+ * no history. Synchronises the handle's stream. */
+SSTEP_API sstep_status sstep_cg_history(sstep_cg_t handle, double* out_h, int capacity, int* count);
 
 /* Changes the stopping tolerance and the outer-iteration limit of an existing handle (for
  * example a looser tolerance for an adjoint solve that reuses the forward handle). */

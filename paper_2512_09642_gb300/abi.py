@@ -30,7 +30,8 @@ class Opts(C.Structure):
                 ("precision", C.c_int), ("precond", C.c_int), ("basis_start", C.c_int), ("gram_form", C.c_int),
                 ("refresh_period", C.c_int), ("max_refresh", C.c_int), ("seed", C.c_uint64),
                 ("use_graph", C.c_int), ("check_every", C.c_int), ("profile_every", C.c_int),
-                ("batch_chunk", C.c_int), ("batch_ctas_per_sm", C.c_int), ("block_conjugate", C.c_int)]
+                ("batch_chunk", C.c_int), ("batch_ctas_per_sm", C.c_int), ("block_conjugate", C.c_int),
+                ("history", C.c_int)]
 
 
 class Info(C.Structure):
@@ -91,6 +92,7 @@ _SIGS = {
     "sstep_cg_batch_last_error": (C.c_char_p, [_VP]),
     "sstep_coarse_fgs": (_I, [_VP, _I, _I, _I, _VP, _VP, _I, _I]),
     "sstep_gram_fgs_noalloc": (_I, [_I64, _I, _I, _I, _VP, _I64, _VP, _D, _D, _D, _VP, _VP]),
+    "sstep_cg_history": (_I, [_VP, C.POINTER(C.c_double), _I, C.POINTER(C.c_int)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -312,6 +314,17 @@ def sstep_gram_fgs_noalloc(n, s, nu, gram_solver, P, ldp, mdiag, mconst, lambda_
     st = lib.sstep_gram_fgs_noalloc(int(n), int(s), int(nu), int(gram_solver), _ptr(P), int(ldp), _ptr(mdiag),
                                     float(mconst), float(lambda_min), float(lambda_max), _ptr(out), _stream(stream))
     return _check(st, None)
+
+
+def sstep_cg_history(h, capacity: int):
+    """The last solve's per-outer-iteration records (opts.history > 0): a list of dicts with
+    outer, rel_res_sq (||r_(k-1)||^2 / ||r_0||^2), delta (the Gram solve's inexactness) and
+    min_gii, oldest first."""
+    buf = (C.c_double * (4 * capacity))()
+    cnt = C.c_int(0)
+    _check(lib.sstep_cg_history(h, buf, int(capacity), C.byref(cnt)), h)
+    return [{"outer": int(buf[4 * k]), "rel_res_sq": buf[4 * k + 1], "delta": buf[4 * k + 2],
+             "min_gii": buf[4 * k + 3]} for k in range(cnt.value)]
 
 
 def exported_names():

@@ -37,6 +37,7 @@ struct sstep_cg_s {
     void* mom_part = nullptr;   // their per-block partials, s steps x 16 bytes x mom_nblk
     int mom_nblk = 0;
     double* mom_part2 = nullptr;   // the finish kernel's per-block sums
+    double* hist = nullptr;     // per-outer records (opts.history > 0)
     double* res_partials = nullptr;
     bool conj = false;          // block-conjugated form: P holds P_+, Q_(k-1), A Q_(k-1)
     double* conj_partials = nullptr;
@@ -127,6 +128,7 @@ sstep_status validate_opts(sstep_cg_t h, const sstep_cg_opts* o) {
 
     if (o->check_every < 1) { set_err(h, "check_every < 1"); return SSTEP_ERR_INVALID_ARG; }
     if (o->profile_every < 0) { set_err(h, "profile_every < 0"); return SSTEP_ERR_INVALID_ARG; }
+    if (o->history < 0 || o->history > (1 << 20)) { set_err(h, "history outside [0, 2^20]"); return SSTEP_ERR_INVALID_ARG; }
     return SSTEP_OK;
 }
 
@@ -345,9 +347,12 @@ GramArgs gram_args(sstep_cg_t h) {
     return g;
 }
 
-// The same, with the block-conjugated form's inputs (used by the outer iteration only).
+// The same, with the block-conjugated form's inputs and the record ring (used by the outer
+// iteration only).
 GramArgs gram_args_outer(sstep_cg_t h) {
     GramArgs g = gram_args(h);
+    g.hist = h->hist;
+    g.hist_cap = h->opts.history;
     if (h->conj) {
         g.conj = 1;
         g.conj_nblk = h->conj_nblk;
@@ -412,6 +417,10 @@ sstep_status finish_create(sstep_cg_t h) {
         if ((st = make_f32_operator(h)) != SSTEP_OK) return st;
     }
     CK(cudaMalloc(&h->rtrue, sizeof(double) * n));
+    if (h->opts.history > 0) {
+        CK(cudaMalloc(&h->hist, sizeof(double) * 4 * h->opts.history));
+        CK(cudaMemsetAsync(h->hist, 0, sizeof(double) * 4 * h->opts.history, h->stream));
+    }
     if (h->fused) {
         // the step kernels reduce the moments: a stencil operator with a constant M (Poisson
         // star or box stencil, or no preconditioner)
@@ -986,6 +995,7 @@ sstep_status sstep_cg_destroy(sstep_cg_t h) {
     cudaFree(h->gram_partials);
     cudaFree(h->mom_part);
     cudaFree(h->mom_part2);
+    cudaFree(h->hist);
     cudaFree(h->res_partials);
     cudaFree(h->conj_partials);
     cudaFree(h->cj);
@@ -1095,6 +1105,29 @@ sstep_status sstep_convert_check(const double* in_d, int k, float* out_d, double
         sstep::set_global_error(cudaGetErrorString(e));
         return SSTEP_ERR_CUDA;
     }
+    return SSTEP_OK;
+}
+
+sstep_status sstep_cg_history(sstep_cg_t h, double* out_h, int capacity, int* count) {
+    if (!h || !out_h || capacity < 1 || !count) return SSTEP_ERR_INVALID_ARG;
+    *count = 0;
+    if (!h->hist) {
+        set_err(h, "the handle keeps no history (opts.history = 0)");
+        return SSTEP_ERR_INVALID_ARG;
+    }
+    sstep_status st = read_ctl(h);
+    if (st != SSTEP_OK) return st;
+    const int cap = h->opts.history, outer = h->ctl_h->outer;
+    int m = outer < cap ? outer : cap;
+    if (m > capacity) m = capacity;
+    std::vector<double> ring((size_t)4 * cap);
+    CK(cudaMemcpyAsync(ring.data(), h->hist, sizeof(double) * 4 * cap, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < m; ++k) {   // the newest m records, oldest first
+        const int o = outer - m + k;   // 0-based outer index
+        for (int q = 0; q < 4; ++q) out_h[4 * k + q] = ring[(size_t)4 * (o % cap) + q];
+    }
+    *count = m;
     return SSTEP_OK;
 }
 

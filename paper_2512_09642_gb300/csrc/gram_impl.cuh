@@ -243,6 +243,9 @@ struct GramParams {
     int conj, conj_nblk;
     const double* conj_partials;
     double* cj;
+    int fp32;                    // the basis is the mixed form's scaled FP32 copy
+    double* hist;                // per-outer record ring (outer, ||r||^2 / ||r_0||^2, delta, min G_ii)
+    int hist_cap;
 };
 
 // nu forward Gauss-Seidel sweeps on one right-hand side, lane j owning row j (lanes >= S and
@@ -403,6 +406,10 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     const int lane = threadIdx.x;   // warp 0 only
     constexpr int NSYM = S * (S + 1) / 2;
     constexpr int NW = MOM ? 2 * S : NSYM + S;   // where the unweighted c entries start
+    // the control block's inputs, read once up front (independent loads whose latency the
+    // assembly of G hides; every lane takes the same decisions from them)
+    const double c_scale = ctl->scale, c_r0 = ctl->r0_sq, c_tol = ctl->tol_sq, c_ming = ctl->min_gii;
+    const int c_outer = ctl->outer, c_maxo = ctl->max_outer;
     double* Gs = sm;                // G~, row-major S x S
     double* cs = sm + S * S;        // c~
     double* ds = cs + S;            // d
@@ -443,21 +450,23 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     __syncwarp();
     // c_0 = ||p_0||^2; the mixed form's FP32 p_0 carries the power-of-two scale of its outer
     // iteration, which the stopping test between FP64 refreshes (check 2) takes out
-    const double rk_sq = gp.check == 2 ? cs[0] / (ctl->scale * ctl->scale) : cs[0];
-    if (lane == 0) {
+    const double cs0 = cs[0];   // c_0 = ||p_0||^2 before the scaling (kept for the record)
+    const double rk_sq = gp.check == 2 ? cs0 / (c_scale * c_scale) : cs0;
+    {
         int done = RUNNING;
         if (!(rk_sq >= 0.0) || !isfinite(rk_sq)) done = NUMERICAL;
         if (gp.check) {
-            ctl->rk_sq = rk_sq;
-            if (done == RUNNING && (ctl->r0_sq == 0.0 || rk_sq < ctl->tol_sq * ctl->r0_sq)) done = CONVERGED;
-            else if (done == RUNNING && ctl->outer >= ctl->max_outer) done = MAX_OUTER;
+            if (done == RUNNING && (c_r0 == 0.0 || rk_sq < c_tol * c_r0)) done = CONVERGED;
+            else if (done == RUNNING && c_outer >= c_maxo) done = MAX_OUTER;
         } else if (done == RUNNING && rk_sq == 0.0) {
             done = CONVERGED;   // the refreshed residual rounded to zero in FP32
         }
-        ctl->done = done;
+        if (lane == 0) {
+            if (gp.check) ctl->rk_sq = rk_sq;
+            ctl->done = done;
+        }
+        if (done != RUNNING) return;
     }
-    __syncwarp();
-    if (ctl->done != RUNNING) return;
     if constexpr (S <= 16) {
         if (totc) {
             conj_transform<S>(Gs, cs, totc, gp, ctl, cscr);
@@ -482,7 +491,7 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     for (int idx = lane; idx < S * S; idx += 32) finite &= (bool)isfinite(Gs[idx]);
     if (lane < S) finite &= (bool)isfinite(cs[lane]);
     finite = __all_sync(0xffffffffu, finite);
-    if (lane == 0) ctl->min_gii = fmin(ctl->min_gii, mg);
+    if (lane == 0) ctl->min_gii = fmin(c_ming, mg);
     if (kept == 0u || !finite) {
         if (lane == 0) ctl->done = NUMERICAL;
         return;
@@ -576,8 +585,17 @@ __device__ void gram_finish(const double* tot, const GramParams& gp, Ctl* ctl, d
     }
     for (int idx = lane; idx < S * S; idx += 32) ctl->Gt[idx] = Gs[idx];
     if (lane == 0) {
-        ctl->delta = cn > 0.0 ? sqrt(res / cn) : 0.0;
-        ctl->outer += 1;
+        const double delta = cn > 0.0 ? sqrt(res / cn) : 0.0;
+        ctl->delta = delta;
+        ctl->outer = c_outer + 1;
+        if (gp.hist) {
+            const double r2 = gp.fp32 ? cs0 / (c_scale * c_scale) : cs0;
+            double* rec = gp.hist + 4 * (size_t)(c_outer % gp.hist_cap);
+            rec[0] = (double)(c_outer + 1);
+            rec[1] = c_r0 > 0.0 ? r2 / c_r0 : 0.0;
+            rec[2] = delta;
+            rec[3] = mg;
+        }
         if (totc) ctl->conj_valid = 1;
     }
 }
@@ -674,6 +692,9 @@ inline GramParams gram_params(const GramArgs& g) {
     gp.conj_nblk = g.conj_nblk;
     gp.conj_partials = g.conj_partials;
     gp.cj = g.cj;
+    gp.fp32 = g.fp32 ? 1 : 0;
+    gp.hist = g.hist;
+    gp.hist_cap = g.hist_cap;
     return gp;
 }
 
@@ -734,13 +755,21 @@ __global__ void __launch_bounds__(FIN_THREADS) k_moments_finish(const T* __restr
         // (2 q + c) nblk (FP64: q nblk)
         const int j = v >> 1, q = v & 1;
         const T* base = part + (size_t)(2 * j + q) * NC * nblk;
+        auto val = [&](int b) -> double {
+            if constexpr (NC == 2) return f2d_exact(__ldg(base + b)) + f2d_exact(__ldg(base + nblk + b));
+            else return __ldg(base + b);
+        };
         double acc = 0.0;
-        for (int b = lo + lane; b < hi; b += 32) {
-            double x;
-            if constexpr (NC == 2) x = f2d_exact(__ldg(base + b)) + f2d_exact(__ldg(base + nblk + b));
-            else x = __ldg(base + b);
-            acc += x;
+        int b = lo + lane;
+        // eight values per lane in flight at once, summed in the order of b
+        for (; b + 7 * 32 < hi; b += 8 * 32) {
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = val(b + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += x[u];
         }
+        for (; b < hi; b += 32) acc += val(b);
         acc = warp_sum(acc);
         if (lane == 0) part2[(size_t)blockIdx.x * NV + v] = acc;
     }

@@ -110,16 +110,16 @@ __device__ __forceinline__ void mom_block_store(const MomAcc<float>& m, void* pa
     }
     __syncthreads();
     if (w == 0) {
-        // the block's warps, lane k holding warp k's pairs: a 3-level butterfly over lanes 0..7
+        // the block's warps, lane k holding warp k's pairs: a butterfly over lanes 0..NW-1
         constexpr int NW = BX * BY / 32;
-        static_assert(NW == 8, "the combine below assumes 8 warps per block");
+        static_assert(NW >= 2 && NW <= 32 && (NW & (NW - 1)) == 0, "warps per block: a power of 2 up to 32");
         const bool has = lane < NW;
         ah = has ? sh[lane][0] : 0.f;
         al = has ? sh[lane][1] : 0.f;
         bh = has ? sh[lane][2] : 0.f;
         bl = has ? sh[lane][3] : 0.f;
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
+        for (int o = NW / 2; o > 0; o >>= 1) {
             pair_add(ah, al, __shfl_xor_sync(0xffffffffu, ah, o), __shfl_xor_sync(0xffffffffu, al, o));
             pair_add(bh, bl, __shfl_xor_sync(0xffffffffu, bh, o), __shfl_xor_sync(0xffffffffu, bl, o));
         }

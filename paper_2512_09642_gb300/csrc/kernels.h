@@ -67,6 +67,9 @@ struct GramArgs {
     // stopping test in the Gram finish: 0 none (the mixed form's FP64 refresh tests), 1 on
     // c_0 = ||r_k||^2, 2 on c_0 / scale^2 (mixed form, outer iterations without a refresh)
     int check;
+    // per-outer record ring (hist_cap records of 4 doubles), or null
+    double* hist;
+    int hist_cap;
     double theta, sigma;
     bool dvec;                 // D is the vector op.diag (else the constant op.dconst)
     double dconst;

@@ -70,3 +70,25 @@ def test_stored_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(fake_root))
     assert bench.kernel_source_sha(src, kernel) not in (None, sha)
     assert bench.measured_traffic("poisson3d_7pt_256^3", "fp64+mom", "cheb_step") is None
+
+
+def test_fused_csr_and_refresh_models():
+    """The fused moments move the Gram's FMAs into the steps (2 per unknown and step in FP64)
+    and leave the finish no streaming bytes; the mixed update writes the recursive residual
+    (reads p_s, writes p_0: 8 B more) in refresh_period - 1 of every refresh_period outer
+    iterations, and the FP64 refresh runs once per period; a CSR step reads 12 B per nonzero
+    (8 B in the mixed form) plus the row pointer and four vectors."""
+    f = bench.kernel_model(8, fused=True)
+    assert f["cheb_step"] == {"ops": 9, "bytes": 24} and f["gram_fgs"] == {"ops": 0, "bytes": 0}
+    fm = bench.kernel_model(8, mixed=True, fused=True)
+    assert fm["cheb_step"] == {"ops": 0, "bytes": 12} and fm["gram_fgs"]["bytes"] == 0
+    assert bench.kernel_model(8, mixed=True, write_r=True)["update"]["bytes"] == 4 * 8 + 16 + 8
+    # mixed, fused, refresh every 4: steps 8 + 7 x 12, update 48 + 8 x 3/4, refresh 20 / 4
+    assert bench.outer_bytes(8, mixed=True, fused=True, refresh=4) == 8 + 7 * 12 + 48 + 6 + 5
+    assert bench.outer_bytes(8, mixed=True, fused=True, refresh=1) == 8 + 7 * 12 + 48 + 20
+    c = bench.kernel_model(8, csr=7.0)
+    assert c["cheb_step"] == {"ops": 9.0, "bytes": 12 * 7.0 + 4 + 24 + 8}
+    cm = bench.kernel_model(8, mixed=True, csr=7.0)
+    assert cm["cheb_step"] == {"ops": 0, "bytes": 8 * 7.0 + 4 + 12 + 4}
+    assert bench.form_gram("mixed+fused+r8") == "fused" and bench.form_refresh("mixed+fused+r8") == 8
+    assert bench.form_gram("fp64+mom") == "moments" and bench.form_refresh("fp64") == 1

@@ -334,3 +334,46 @@ def test_fused_form_rejects_operators_without_constant_m():
     x, info = sv.solve(_dev(p.b))
     assert info["outer_iters"] == 3
     assert _rel(x.cpu().numpy(), ref.history[2].x) <= 1e-10
+
+
+@pytest.mark.parametrize("form,precision", [("moments", "fp64"), ("fused", "fp64"), ("direct", "fp64"),
+                                            ("fused", "mixed")])
+def test_per_outer_history_records(form, precision):
+    """opts.history keeps, per outer iteration, ||r_(k-1)||^2 / ||r_0||^2 of the residual the
+    iteration starts from, the Gram solve's inexactness delta_k and the smallest G_ii: the
+    residual norms match the oracle's iterates (FP64: 1e-9 relative; mixed: the FP32 level),
+    delta_k matches the oracle's ||c~ - G~ a|| / ||c~|| of its own FGS solve, and a ring smaller
+    than the solve keeps its newest records."""
+    from paper_2512_09642_gb300 import abi
+    p = W.poisson3d(24)
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+    ref = O.solve(op, p.b, s=8, nu=25, lam_min=lam[0], lam_max=lam[1], tol=1e-30, max_outer=6, history=6)
+    r0 = np.linalg.norm(p.b)
+    sv = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-30, max_outer=6, check_every=1, gram_form=form,
+                 precision=precision, history=64)
+    x, info = sv.solve(_dev(p.b))
+    recs = abi.sstep_cg_history(sv.h, 64)
+    assert [r["outer"] for r in recs] == list(range(1, 7))
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    for k, rec in enumerate(recs):
+        r_prev = p.b if k == 0 else ref.history[k - 1].r
+        want = (np.linalg.norm(r_prev) / r0) ** 2
+        assert abs(rec["rel_res_sq"] - want) <= tol * want, (k, rec, want)
+        assert 0.0 <= rec["delta"] < 1.0 and rec["min_gii"] > 0.0
+    # the oracle's inexactness of its own Gram solve at the first outer iteration
+    Pp = O.chebyshev_basis(op, p.b, 8, lam[0], lam[1])
+    G, c, _ = O.gram(op, Pp, p.b)
+    d, Gt, ct = O.column_scaling(G, c)
+    a = O.fgs(Gt, ct, 25)
+    delta0 = np.linalg.norm(ct - Gt @ a) / np.linalg.norm(ct)
+    assert abs(recs[0]["delta"] - delta0) <= (1e-6 if precision == "fp64" else 5e-2) * delta0
+    sv.close()
+    small = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-30, max_outer=6, check_every=1, gram_form=form,
+                    precision=precision, history=4)
+    small.solve(_dev(p.b))
+    assert [r["outer"] for r in abi.sstep_cg_history(small.h, 10)] == [3, 4, 5, 6]
+    assert [r["outer"] for r in abi.sstep_cg_history(small.h, 2)] == [5, 6]
+    plain = _solver(p, "stencil", bounds=lam, s=8)
+    with pytest.raises(abi.SStepError):
+        abi.sstep_cg_history(plain.h, 4)
