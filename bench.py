@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--forms", default=parse_default_forms(),
                     help="comma list of fp64, mixed, fp64+mom, mixed+mom, fp64+mom+conj (+mom: Gram from "
                          "Chebyshev moments; +conj: block-conjugated s-step CG); the first is the headline")
-    ap.add_argument("--graph", action="store_true", help="run the outer loop as one CUDA graph (no kernel sampling)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="time the host-driven outer loop (convergence read every 8 outer iterations) instead of "
+                         "the CUDA-graph loop; the per-kernel sampling then runs inside the timed solves")
     ap.add_argument("--workload", default="poisson3d",
                     choices=["poisson3d", "poisson27", "poisson2d_64", "diffusion3d", "batch", "coarse", "sweep",
                              "spread", "adjoint"],
@@ -450,32 +452,40 @@ def run_reference(args):
 
 
 def measure_form(args, p, b, world, local, precision, csr=None, fixed_outers=None, e2e=True):
-    """Warm-up + K timed solves of one form; per-kernel durations from the sampled events.
-    fixed_outers: run exactly that many outer iterations per solve (tol 1e-30), sampling the
-    kernels in every chunk of 8, and skip the end-to-end leg."""
+    """Warm-up + K timed solves of one form, the outer loop as one CUDA graph (the library's
+    fastest way to run it; --host-loop times the host-driven loop instead); then one more
+    solve with the host loop and CUDA events around every kernel of sampled outer iterations,
+    for the per-kernel durations (kernels cannot be timed one by one inside a graph).
+    fixed_outers: run exactly that many outer iterations per solve (tol 1e-30) with the host
+    loop, sampling the kernels in every chunk of 8, and skip the end-to-end leg."""
     import torch
     from paper_2512_09642_gb300 import SStepCG, abi
 
     n, s = p.n, args.s
     parts = precision.split("+")
     prec = parts[0]
-    kw = dict(s=s, nu=args.nu, tol=1e-8, check_every=8, profile_every=0 if args.graph else 4, precision=prec,
-              gram_form=form_gram(precision), use_graph=1 if args.graph else 0,
+    graph = not args.host_loop and not fixed_outers
+    kw = dict(s=s, nu=args.nu, tol=1e-8, check_every=8, profile_every=0 if graph else 4, precision=prec,
+              gram_form=form_gram(precision), use_graph=1 if graph else 0,
               block_conjugate=1 if "conj" in parts else 0, refresh_period=form_refresh(precision))
     if fixed_outers:
         kw.update(tol=1e-30, max_outer=int(fixed_outers), profile_every=1)
     if p.stencil == "box":
         kw["bounds_mode"] = "lanczos10"   # Section 8: Lanczos-10 estimates of both ends, 10% margins
-    if csr is not None:
-        sv = SStepCG(csr=csr, **kw)
-    else:
-        sv = SStepCG(grid=p.dims, kappa=None if p.kappa is None else torch.as_tensor(p.kappa).cuda(),
-                     stencil=p.stencil, **kw)
+    kappa = None if p.kappa is None else torch.as_tensor(p.kappa).cuda()
+
+    def make(**extra):
+        o = dict(kw, **extra)
+        if csr is not None:
+            return SStepCG(csr=csr, **o)
+        return SStepCG(grid=p.dims, kappa=kappa, stencil=p.stencil, **o)
+
+    sv = make()
     stream = torch.cuda.current_stream()
 
-    def one_solve():
+    def one_solve(h=None):
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
-        info = abi.sstep_cg_solve(sv.h, b, x)
+        info = abi.sstep_cg_solve((h or sv).h, b, x)
         return x, info.as_dict()
 
     for _ in range(args.warmup):
@@ -510,7 +520,15 @@ def measure_form(args, p, b, world, local, precision, csr=None, fixed_outers=Non
             times.append(time.perf_counter() - t0)
         t_e2e = max_over_ranks(statistics.mean(times), world)
     sv.close()
-    return {"t": t_solve, "e2e": t_e2e, "infos": infos, "clocks": clk, "x": x}
+    prof_infos = infos
+    if graph:
+        # per-kernel durations: one host-loop solve with every chunk's second outer iteration sampled
+        sp = make(use_graph=0, profile_every=1)
+        one_solve(sp)
+        prof_infos = [one_solve(sp)[1]]
+        sp.close()
+    return {"t": t_solve, "e2e": t_e2e, "infos": infos, "prof_infos": prof_infos, "clocks": clk, "x": x,
+            "graph": graph}
 
 
 def kernel_report(args, n, infos, precision, dim=3, diffusion=False, box=False, csr=None):
@@ -604,10 +622,8 @@ def run_ours(args):
         r = measure_form(args, p, b, world, local, prec, csr, e2e=prec == args.forms.split(",")[0])
         dim = len(p.dims)
         diff = p.kappa is not None
-        # (graph runs report times only: no kernel sampling inside a graph)
         nnz_row = None if csr is None else float(csr[0][-1].item()) / n
-        roof, table = (kernel_report(args, n, r["infos"], prec, dim, diff, box, nnz_row) if not args.graph
-                       else ({}, {}))
+        roof, table = kernel_report(args, n, r["prof_infos"], prec, dim, diff, box, nnz_row)
         info = r["infos"][-1]
         outers = info["outer_iters"]
         cj = "+conj" in prec
@@ -643,14 +659,14 @@ def run_ours(args):
             h["roofline"]["traffic_source"] = f"ncu capture of {tr['kernel']}, profiles/{tr['profile']}"
 
     spread = None
-    if args.workload == "poisson3d" and csr is None and not args.no_spread and not args.graph:
+    if args.workload == "poisson3d" and csr is None and not args.no_spread:
         # the headline form on the five seeded x* (the first is the workload's): the outer
         # count to 1e-8 of this restarted iteration moves with rounding, the time per outer
         # iteration does not
         from paper_2512_09642_gb300 import SStepCG, abi
         parts = head.split("+")
         sv = SStepCG(grid=p.dims, s=s, nu=nu, tol=1e-8, check_every=8, precision=parts[0], gram_form=form_gram(head),
-                     block_conjugate=1 if "conj" in parts else 0,
+                     block_conjugate=1 if "conj" in parts else 0, use_graph=0 if args.host_loop else 1,
                      refresh_period=form_refresh(head) if parts[0] == "mixed" else 1)
         runs = []
         for sd in SPREAD_SEEDS:
@@ -712,7 +728,7 @@ def run_ours(args):
             "dtype": "f64" if head.startswith("fp64") else "f32 basis + f64 Gram/x/residual",
             "data": f"synthetic (b = A x*, x* ~ U(-1,1) splitmix64 seed {1000 + p.meta['config']})",
             "config": cfg,
-            "form": head, "graph": bool(args.graph), "parallelism": f"replicas x{world}",
+            "form": head, "graph": not args.host_loop, "parallelism": f"replicas x{world}",
             "outer_iters": h["outer_iters"], "rel_res_true": h["rel_res_true"], "outer_per_s": h["outer_per_s"],
             "hbm_gbs_model": h["hbm_gbs_model"], "roofline": h["roofline"],
             "e2e": {"value": h["e2e_s"], "unit": "s", "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
@@ -938,7 +954,8 @@ def run_spread(args):
         for form in forms:
             parts = form.split("+")
             sv = SStepCG(grid=probs[0].dims, s=8, nu=25, tol=1e-8, check_every=8, precision=parts[0],
-                         gram_form=form_gram(form), refresh_period=form_refresh(form) if parts[0] == "mixed" else 1)
+                         gram_form=form_gram(form), refresh_period=form_refresh(form) if parts[0] == "mixed" else 1,
+                         use_graph=0 if args.host_loop else 1)
             x = torch.zeros(probs[0].n, dtype=torch.float64, device="cuda")
             for _ in range(max(args.warmup, 1)):
                 x.zero_()

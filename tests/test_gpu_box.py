@@ -89,7 +89,7 @@ def test_box_gram_solve_matches_oracle(form, s):
 
 
 @pytest.mark.parametrize("dims,cfg,s,nu", [((37, 19, 21), 31, 8, 25), ((70, 45), 32, 4, 20), ((33, 9, 16), 33, 12, 30)])
-@pytest.mark.parametrize("form", ["direct", "moments"])
+@pytest.mark.parametrize("form", ["direct", "moments", "fused"])
 def test_box_per_iterate_parity_first_five_outer_iterations(dims, cfg, s, nu, form):
     p = _prob(dims, cfg)
     op = O.Operator(*p.csr())
@@ -123,15 +123,36 @@ def test_box_full_solve_matches_oracle(form, use_graph):
     assert _rel(x, ref.x) <= 1e-7
 
 
-def test_box_mixed_precision_reaches_tolerance():
-    p = _prob((37, 19, 21), 31)
+# odd nx: one point per thread in the FP32 box step; even nx: two x-adjacent points per thread
+@pytest.mark.parametrize("dims,cfg", [((37, 19, 21), 31), ((70, 13, 11), 34), ((2, 9, 5), 35), ((64, 45), 36)])
+@pytest.mark.parametrize("form,period", [("moments", 1), ("fused", 1), ("fused", 4)])
+def test_box_mixed_precision_reaches_tolerance(dims, cfg, form, period):
+    p = _prob(dims, cfg)
     op = O.Operator(*p.csr())
-    sv = _box(p, bounds_mode="lanczos10", s=8, nu=25, tol=1e-8, gram_form="moments", precision="mixed")
+    sv = _box(p, bounds_mode="lanczos10", s=8, nu=25, tol=1e-8, gram_form=form, precision="mixed",
+              refresh_period=period)
     x, info = sv.solve(_dev(p.b))
     x = x.cpu().numpy()
     assert info["status"] == "SSTEP_OK"
     assert np.linalg.norm(p.b - op.matvec(x)) / np.linalg.norm(p.b) <= 1e-8
     assert _rel(x, p.x_star) <= 1e-5
+
+
+@pytest.mark.parametrize("dims,cfg", [((37, 19, 21), 31), ((70, 13, 11), 34), ((64, 45), 36)])
+def test_box_mixed_first_iterates_at_fp32_level(dims, cfg):
+    """The FP32 box step (one or two points per thread) against the FP64 oracle's first two
+    iterates, to the FP32 level."""
+    p = _prob(dims, cfg)
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "lanczos10", W.lanczos_start(p.n))
+    ref = O.solve(op, p.b, s=8, nu=25, lam_min=lam[0], lam_max=lam[1], tol=1e-30, max_outer=2, history=2)
+    for k in (1, 2):
+        sv = _box(p, bounds=lam, s=8, nu=25, tol=1e-30, max_outer=k, check_every=1, gram_form="fused",
+                  precision="mixed")
+        x, info = sv.solve(_dev(p.b))
+        assert info["outer_iters"] == k
+        assert _rel(x.cpu().numpy(), ref.history[k - 1].x) <= 1e-5, (dims, k)
+        sv.close()
 
 
 @pytest.mark.parametrize("dims", [(12, 11, 10), (2, 7, 3), (1, 13, 1), (9, 4)])

@@ -355,7 +355,7 @@ def test_per_outer_history_records(form, precision):
     x, info = sv.solve(_dev(p.b))
     recs = abi.sstep_cg_history(sv.h, 64)
     assert [r["outer"] for r in recs] == list(range(1, 7))
-    tol = 1e-9 if precision == "fp64" else 1e-5
+    tol = 1e-9 if precision == "fp64" else 1e-4   # mixed: its iterates differ from FP64's at the FP32 level
     for k, rec in enumerate(recs):
         r_prev = p.b if k == 0 else ref.history[k - 1].r
         want = (np.linalg.norm(r_prev) / r0) ** 2
