@@ -877,7 +877,8 @@ def run_coarse(args):
 
 def run_sweep(args):
     """Bandwidth sweep on 3D Poisson (7-point, 512^3 = 134M unknowns by default) over s in
-    {4, 8, 12, 16}, FP64 and mixed forms (moments Gram): each solve runs a fixed number of
+    {4, 8, 12, 16}, FP64 (moments Gram) and mixed (fused moments, FP64 refresh every 8) forms,
+    host-driven loop: each solve runs a fixed number of
     outer iterations, and every kernel's CUDA-event time, sampled inside them, gives its
     algorithmic GB/s and FP64 rate against the HBM and FP64-pipe roofs."""
     import torch
@@ -892,12 +893,13 @@ def run_sweep(args):
     rows = []
     for s in (4, 8, 12, 16):
         args.s = s
-        for prec in ("fp64+mom", "mixed+mom"):
+        for prec in ("fp64+mom", "mixed+fused+r8"):
             r = measure_form(args, p, b, world, local, prec, fixed_outers=args.sweep_outers)
             roof, table = kernel_report(args, n, r["infos"], prec)
             outers = r["infos"][-1]["outer_iters"]
             per_outer = r["t"] / outers
-            ob = outer_bytes(s, prec.startswith("mixed"), 3) * n
+            ob = outer_bytes(s, prec.startswith("mixed"), 3, fused=form_gram(prec) == "fused",
+                             refresh=form_refresh(prec) if prec.startswith("mixed") else 1) * n
             rows.append({"s": s, "form": prec, "outer_iters": outers, "ms_per_outer": per_outer * 1e3,
                          "model_bytes_per_outer": ob, "hbm_gbs_model": ob / per_outer / 1e9,
                          "dominant": {k: roof[k] for k in ("kernel", "bound", "frac", "alu_frac", "hbm_frac")},
