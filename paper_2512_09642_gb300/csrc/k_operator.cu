@@ -72,9 +72,10 @@ __device__ __forceinline__ void pair_add(float& h, float& l, float h2, float l2)
 }
 
 // Block reduction of the accumulators and the store of this block's partials. Every thread
-// of the block calls it (blocks of BX x BY threads, any grid shape).
+// of the block calls it (blocks of NT threads, 32 in x; any grid shape).
+template <int NT = BX * BY>
 __device__ __forceinline__ void mom_block_store(const MomAcc<double>& m, void* part, int nblk) {
-    __shared__ double sh[BX * BY / 32][2];
+    __shared__ double sh[NT / 32][2];
     const int t = threadIdx.x + BX * threadIdx.y, lane = t & 31, w = t >> 5;
     // lanes of even index carry a, odd ones b after the first exchange: one FP64 add per level
     double v = (lane & 1) ? m.b : m.a;
@@ -87,7 +88,7 @@ __device__ __forceinline__ void mom_block_store(const MomAcc<double>& m, void* p
     if (t < 2) {
         double acc = sh[0][t];
 #pragma unroll
-        for (int k = 1; k < BX * BY / 32; ++k) acc += sh[k][t];
+        for (int k = 1; k < NT / 32; ++k) acc += sh[k][t];
         const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
         ((double*)part)[(size_t)t * nblk + blk] = acc;
     }
@@ -728,6 +729,174 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_box_f32_pair(const float* __res
     if (GRAM) mom_block_store(acc, mom, nblk);
 }
 
+// FP64 box step, register-blocked and persistent (3D, nx even, 16-byte aligned vectors). A
+// thread owns two x-adjacent points (one 16-byte load per row) in BOXY consecutive rows; the
+// lanes run over (row group, x pair) with the pair fastest, so a warp has idle lanes only in
+// the grid's last 32 (a warp's FP64 instruction costs the same whatever its active lanes:
+// 64-point tiles idled 10% of the lanes at nx = 230). A warp column is 32 consecutive lanes
+// of that order; the grid is the resident blocks, and each warp marches an equal contiguous
+// range of the (warp column, plane) units, no shared memory and no barrier. Per plane it
+// loads its BOXY + 2 rows and forms
+//  * the pair's x row sums p(i-1) + (p(i) + p(i+1)) and (p(i) + p(i+1)) + p(i+2): three
+//    additions per pair and row, the outer neighbours from the adjacent lanes by shuffles
+//    (from memory where the adjacent lane holds another row group or lies outside the warp,
+//    0 at the grid's x faces);
+//  * the in-plane sums S of two consecutive rows at a time, which share their middle two row
+//    sums: S(t) = R(t-1) + (R(t) + R(t+1)), S(t+1) = (R(t) + R(t+1)) + R(t+2);
+// 3.75 FP64 additions per point and plane for S at BOXY = 4 (4 plus the tile's halo rows
+// when the row sums go through shared memory). B(k) = S(k-1) + S(k) + S(k+1) is accumulated
+// forward as each plane's S arrives (2 additions per point) and the step adds its 2 FMAs:
+// with a range's two halo planes about 8.1 FP64 instructions per point against about 10.4
+// for k_cheb_box, whose two barriers per plane also leave the FP64 pipe idle. Measured at
+// 230^3: 0.255 -> 0.186 ms per step (0.61 -> 0.83 of the FP64 FMA rate by the 8 operations
+// of the separable sum); tiles of 64 x 16 x 16 points in a plain grid gave 0.246 ms (1.7
+// waves of resident blocks), the same persistent march over 64-point tiles 0.205 ms.
+constexpr int BOXY = 4;   // rows per thread (even)
+constexpr int BOXW = 4;   // warps per block
+
+// The thread's place in the flattened order for warp column c.
+struct BoxLane {
+    int i, jb;                        // first x of the pair, first row
+    bool valid;                       // the lane has a pair
+    bool lload, rload, lzero, rzero;  // outer neighbours: loaded / 0 (x faces) / from a lane
+};
+
+__device__ __forceinline__ BoxLane box_lane(int64_t c, int nx, int ny, int Y) {
+    const int lane = threadIdx.x;
+    const int np = nx / 2;
+    const int64_t nl = (int64_t)np * ((ny + Y - 1) / Y);
+    const int64_t L = c * 32 + lane;
+    BoxLane b;
+    b.valid = L < nl;
+    const int xp = b.valid ? (int)(L % np) : 0;
+    b.i = 2 * xp;
+    b.jb = b.valid ? (int)(L / np) * Y : 0;
+    b.lzero = xp == 0;
+    b.rzero = xp == np - 1;   // also every lane whose next lane is past the last pair
+    b.lload = b.valid && !b.lzero && lane == 0;
+    b.rload = b.valid && !b.rzero && lane == 31;
+    return b;
+}
+
+// S(k), the 3 x 3 in-plane sums of plane k at the thread's 2 x Y points (0 outside the grid);
+// c receives the centre pairs of the Y rows.
+template <int Y>
+__device__ __forceinline__ void box_reg_plane(const double* __restrict__ p, int nx, int ny, int nz, int k,
+                                              const BoxLane& b, double one, double2 (&c)[Y], double (&S)[Y][2]) {
+    const bool kv = k >= 0 && k < nz;
+    double2 v[Y + 2];
+    double el[Y + 2], er[Y + 2];
+#pragma unroll
+    for (int r = 0; r < Y + 2; ++r) {
+        const int jj = b.jb - 1 + r;
+        const bool rv = b.valid && kv && jj >= 0 && jj < ny;
+        const int64_t off = rv ? (int64_t)nx * ny * k + (int64_t)nx * jj + b.i : 0;
+        v[r] = rv ? __ldg(reinterpret_cast<const double2*>(p + off)) : make_double2(0.0, 0.0);
+        el[r] = (rv && b.lload) ? ldg(p + off - 1) : 0.0;
+        er[r] = (rv && b.rload) ? ldg(p + off + 2) : 0.0;
+    }
+    double R[Y + 2][2];
+#pragma unroll
+    for (int r = 0; r < Y + 2; ++r) {
+        double l = __shfl_up_sync(0xffffffffu, v[r].y, 1);
+        double rr = __shfl_down_sync(0xffffffffu, v[r].x, 1);
+        if (b.lload || b.lzero) l = el[r];
+        if (b.rload || b.rzero) rr = er[r];
+        const double m = add1(v[r].x, v[r].y, one);
+        R[r][0] = add1(l, m, one);
+        R[r][1] = add1(m, rr, one);
+    }
+#pragma unroll
+    for (int t = 0; t < Y; ++t) c[t] = v[t + 1];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int t = 0; t < Y; t += 2) {
+            const double m = add1(R[t + 1][x], R[t + 2][x], one);
+            S[t][x] = add1(R[t][x], m, one);
+            S[t + 1][x] = add1(m, R[t + 3][x], one);
+        }
+}
+
+// The warp's share of the persistent march: calls pre(k, row, i) one plane sum ahead of
+// emit(k, row, i, pc, B, pre value) for each of the thread's points in the grid (pc, B and the
+// pre value as pairs at x = i, i + 1).
+template <int Y, typename Pre, typename Emit>
+__device__ __forceinline__ void box_reg_sweep(const double* __restrict__ p, int nx, int ny, int nz, double one, Pre pre,
+                                              Emit emit) {
+    static_assert(Y % 2 == 0, "rows per thread: even");
+    const int np = nx / 2;
+    const int64_t nwc = ((int64_t)np * ((ny + Y - 1) / Y) + 31) / 32;   // warp columns
+    const int64_t U = nwc * nz;
+    const int64_t nw = (int64_t)gridDim.x * BOXW, w = (int64_t)blockIdx.x * BOXW + threadIdx.y;
+    int64_t u = U * w / nw;
+    const int64_t u1 = U * (w + 1) / nw;
+    while (u < u1) {
+        const int64_t c = u / nz;
+        const int k0 = (int)(u - c * nz);
+        const int k1 = (int)(k0 + (u1 - u) < (int64_t)nz ? k0 + (u1 - u) : (int64_t)nz);
+        const BoxLane b = box_lane(c, nx, ny, Y);
+        double A0[Y][2], A1[Y][2], S[Y][2];   // A0: S(k-1) + S(k), A1: S(k)
+        double2 pc[Y], pn[Y];
+        box_reg_plane<Y>(p, nx, ny, nz, k0 - 1, b, one, pn, A0);
+        box_reg_plane<Y>(p, nx, ny, nz, k0, b, one, pc, S);
+#pragma unroll
+        for (int t = 0; t < Y; ++t)
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                A0[t][x] = add1(A0[t][x], S[t][x], one);
+                A1[t][x] = S[t][x];
+            }
+        for (int k = k0; k < k1; ++k) {
+            double2 ev[Y];
+#pragma unroll
+            for (int t = 0; t < Y; ++t)
+                ev[t] = (b.valid && b.jb + t < ny) ? pre(k, b.jb + t, b.i) : make_double2(0.0, 0.0);
+            box_reg_plane<Y>(p, nx, ny, nz, k + 1, b, one, pn, S);
+#pragma unroll
+            for (int t = 0; t < Y; ++t) {
+                const double2 B = make_double2(add1(A0[t][0], S[t][0], one), add1(A0[t][1], S[t][1], one));
+                if (b.valid && b.jb + t < ny) emit(k, b.jb + t, b.i, pc[t], B, ev[t]);
+#pragma unroll
+                for (int x = 0; x < 2; ++x) {
+                    A0[t][x] = add1(A1[t][x], S[t][x], one);
+                    A1[t][x] = S[t][x];
+                }
+                pc[t] = pn[t];
+            }
+        }
+        u += k1 - k0;
+    }
+}
+
+template <int Y, bool FIRST, bool GRAM>
+__global__ void __launch_bounds__(32 * BOXW, 3) k_cheb_box_reg(const double* __restrict__ p,
+                                                               const double* __restrict__ q, double* __restrict__ out,
+                                                               int nx, int ny, int nz, double ca, double cb,
+                                                               const Ctl* __restrict__ ctl, double one, void* mom,
+                                                               int nblk) {
+    if (ctl->done) return;
+    const int64_t sxy = (int64_t)nx * ny;
+    MomAcc<double> acc;
+    box_reg_sweep<Y>(
+        p, nx, ny, nz, one,
+        [&](int k, int j, int i) {
+            return FIRST ? make_double2(0.0, 0.0)
+                         : __ldg(reinterpret_cast<const double2*>(q + sxy * k + (int64_t)nx * j + i));
+        },
+        [&](int k, int j, int i, double2 pc, double2 B, double2 qv) {
+            double2 o;
+            o.x = FIRST ? fma(cb, B.x, ca * pc.x) : fma(cb, B.x, fma(ca, pc.x, -qv.x));
+            o.y = FIRST ? fma(cb, B.y, ca * pc.y) : fma(cb, B.y, fma(ca, pc.y, -qv.y));
+            *reinterpret_cast<double2*>(out + sxy * k + (int64_t)nx * j + i) = o;
+            if (GRAM) {
+                acc.add(pc.x, o.x);
+                acc.add(pc.y, o.y);
+            }
+        });
+    if (GRAM) mom_block_store<32 * BOXW>(acc, mom, nblk);
+}
+
 // r = b - A x = b - (3^d x - B) with ||r||^2 (residual modes as k_residual_stencil).
 template <int DIM>
 __global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restrict__ b, const double* __restrict__ x,
@@ -767,6 +936,43 @@ __global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restric
     last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, nblk);
 }
 
+// r = b - A x with ||r||^2 on the register-blocked persistent march of k_cheb_box_reg (3D, nx
+// even, b, x and r 16-byte and r32 8-byte aligned); residual modes as k_residual_stencil.
+__global__ void __launch_bounds__(32 * BOXW, 3) k_residual_box_reg(const double* __restrict__ b,
+                                                                   const double* __restrict__ x,
+                                                                   double* __restrict__ r, float* __restrict__ r32,
+                                                                   int nx, int ny, int nz, double* partials, Ctl* ctl,
+                                                                   int mode, double one) {
+    if (mode == 2 && ctl->done) return;
+    int kscale = 0;   // scale_next = 2^kscale
+    if (mode == 2) {
+        frexp(ctl->scale_next, &kscale);
+        kscale -= 1;
+    }
+    const int64_t sxy = (int64_t)nx * ny;
+    double ss = 0.0;
+    box_reg_sweep<BOXY>(
+        x, nx, ny, nz, one,
+        [&](int k, int j, int i) { return __ldg(reinterpret_cast<const double2*>(b + sxy * k + (int64_t)nx * j + i)); },
+        [&](int k, int j, int i, double2 pc, double2 B, double2 bv) {
+            const int64_t e = sxy * k + (int64_t)nx * j + i;
+            const double r0 = fma(fma(27.0, pc.x, -B.x), -one, bv.x);   // bv - (27 pc - B)
+            const double r1 = fma(fma(27.0, pc.y, -B.y), -one, bv.y);
+            if (r) *reinterpret_cast<double2*>(r + e) = make_double2(r0, r1);
+            if (r32) *reinterpret_cast<float2*>(r32 + e) = make_float2(d2f_scaled(r0, kscale), d2f_scaled(r1, kscale));
+            ss = fma(r0, r0, ss);
+            ss = fma(r1, r1, ss);
+        });
+    __shared__ double sh[BOXW];
+    const double v = warp_sum(ss);
+    if (threadIdx.x == 0) sh[threadIdx.y] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int k = 0; k < BOXW; ++k) tot += sh[k];
+    last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, (int)gridDim.x);
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(BX* BY) k_apply_box(const double* __restrict__ x, double* __restrict__ y, int nx,
                                                       int ny, int nz) {
@@ -788,6 +994,54 @@ dim3 box_grid(const OpDesc& op) {
 // FP32 box step with two points per thread: nx even and 8-byte aligned vectors
 dim3 box_pair_grid(const OpDesc& op) {
     return dim3((op.nx + 2 * BX - 1) / (2 * BX), (op.ny + BY - 1) / BY, op.dim == 3 ? (op.nz + KBP - 1) / KBP : 1);
+}
+// FP64 register-blocked box step: 3D, nx even and 16-byte aligned vectors. The grid is the
+// blocks resident at once (the fewest over the step's instantiations), at most one warp per
+// (warp column, plane) unit.
+int box_reg_per_sm() {
+    static int per_sm[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!per_sm[dev]) {
+        int m = 1 << 30, b = 0;
+        const int nt = 32 * BOXW;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<BOXY, true, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<BOXY, false, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<BOXY, true, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<BOXY, false, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        per_sm[dev] = (m >= 1 && m < (1 << 30)) ? m : 1;
+    }
+    return per_sm[dev];
+}
+dim3 box_reg_grid(const OpDesc& op) {
+    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + BOXY - 1) / BOXY) + 31) / 32;
+    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
+    const int64_t cap = (int64_t)box_reg_per_sm() * device_sm_count();
+    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
+}
+bool box_reg_ok(const OpDesc& op, const double* p, const double* q, const double* out) {
+    return op.dim == 3 && op.nx % 2 == 0 && ((uintptr_t)p % 16 == 0) && ((uintptr_t)out % 16 == 0) &&
+           (!q || (uintptr_t)q % 16 == 0);
+}
+int box_res_reg_per_sm() {
+    static int per_sm[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!per_sm[dev]) {
+        int b = 0;
+        per_sm[dev] = (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_residual_box_reg, 32 * BOXW, 0) == cudaSuccess && b >= 1) ? b : 1;
+    }
+    return per_sm[dev];
+}
+dim3 box_res_reg_grid(const OpDesc& op) {
+    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + BOXY - 1) / BOXY) + 31) / 32;
+    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
+    const int64_t cap = (int64_t)box_res_reg_per_sm() * device_sm_count();
+    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
+}
+bool box_res_reg_ok(const OpDesc& op, const double* b, const double* x, const double* r, const float* r32) {
+    return op.dim == 3 && op.nx % 2 == 0 && ((uintptr_t)b % 16 == 0) && ((uintptr_t)x % 16 == 0) &&
+           (!r || (uintptr_t)r % 16 == 0) && (!r32 || (uintptr_t)r32 % 8 == 0);
 }
 bool box_pair_ok(const OpDesc& op, const float* p, const float* q, const float* out) {
     return op.nx % 2 == 0 && ((uintptr_t)p % 8 == 0) && ((uintptr_t)out % 8 == 0) && (!q || (uintptr_t)q % 8 == 0);
@@ -893,7 +1147,10 @@ int cheb_step_blocks(const OpDesc& op, bool fp32) {
     if (op.kind != OP_STENCIL) return 0;
     const int kz = fp32 ? kz_step<float>() : kz_step<double>();
     dim3 g;
-    if (op.box) g = fp32 && op.nx % 2 == 0 ? box_pair_grid(op) : box_grid(op);
+    if (op.box) {
+        if (fp32) g = op.nx % 2 == 0 ? box_pair_grid(op) : box_grid(op);
+        else g = op.dim == 3 && op.nx % 2 == 0 ? box_reg_grid(op) : box_grid(op);
+    }
     else if (op.wx == nullptr && op.nx % 2 == 0) g = pair_grid(op, kz);
     else g = stencil_grid(op, kz);
     return (int)(g.x * g.y * g.z);
@@ -908,6 +1165,9 @@ cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, d
         if (!op.box && op.wx == nullptr && op.nx % 2 == 0 && !use_pair(op, p, q, out)) return cudaErrorInvalidValue;
         if (op.box && std::is_same<T, float>::value && op.nx % 2 == 0 &&
             !box_pair_ok(op, (const float*)p, (const float*)q, (const float*)out))
+            return cudaErrorInvalidValue;
+        if (op.box && std::is_same<T, double>::value && op.dim == 3 && op.nx % 2 == 0 &&
+            !box_reg_ok(op, (const double*)p, (const double*)q, (const double*)out))
             return cudaErrorInvalidValue;
     }
     if (op.kind == OP_STENCIL && op.box) {
@@ -934,6 +1194,15 @@ cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, d
             }
 #undef ARGS
             return cudaGetLastError();
+        }
+        if constexpr (std::is_same<T, double>::value) {
+            if (box_reg_ok(op, p, q, out)) {
+                const dim3 g3 = box_reg_grid(op), block(32, BOXW);
+#define ARGS p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl, 1.0
+                SSTEP_STEP_LAUNCH(k_cheb_box_reg, g3, BOXY);
+#undef ARGS
+                return cudaGetLastError();
+            }
         }
 #define ARGS p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl, T(1)
         if (op.dim == 3) SSTEP_STEP_LAUNCH(k_cheb_box, grid, T, 3);
@@ -974,8 +1243,11 @@ template cudaError_t launch_cheb_step<float>(const OpDesc&, const float*, const 
 
 size_t residual_partials_needed(const OpDesc& op) {
     if (op.kind == OP_STENCIL && op.box) {
+        // either kernel may run (the register-blocked one needs aligned vectors)
         const dim3 g = box_grid(op);
-        return (size_t)g.x * g.y * g.z;
+        const size_t n1 = (size_t)g.x * g.y * g.z;
+        if (op.dim != 3 || op.nx % 2 != 0) return n1;
+        return std::max(n1, (size_t)box_res_reg_grid(op).x);
     }
     if (op.kind == OP_STENCIL) {
         const dim3 g = stencil_grid(op, KZ_RES);
@@ -987,6 +1259,11 @@ size_t residual_partials_needed(const OpDesc& op) {
 cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, double* r, float* r32,
                             double* partials, Ctl* ctl, int mode, cudaStream_t st) {
     if (op.kind == OP_STENCIL && op.box) {
+        if (box_res_reg_ok(op, b, x, r, r32)) {
+            k_residual_box_reg<<<box_res_reg_grid(op), dim3(32, BOXW), 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz,
+                                                                               partials, ctl, mode, 1.0);
+            return cudaGetLastError();
+        }
         const dim3 grid = box_grid(op), block(BX, BY);
         if (op.dim == 3) k_residual_box<3><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode, 1.0);
         else k_residual_box<2><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode, 1.0);

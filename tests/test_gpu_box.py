@@ -2,8 +2,10 @@
 experiments in Section 8; 9-point in 2D) against the CPU oracle, which applies the same
 matrix assembled as CSR by the workload generator.
 
-Grids are ragged against every blocking of the kernels (32 x 8 tiles, 16-plane z slabs), and
-the bounds follow Section 8 (Lanczos-10 with 10% margins) unless a test fixes them.
+Grids are ragged against every blocking of the kernels (32 x 8 tiles, 16-plane z slabs; for the
+FP64 3D step and residual with nx even, 32-lane warp columns over (row group of 4, x pair) and
+a persistent split of the (warp column, plane) units over the resident warps), and the bounds
+follow Section 8 (Lanczos-10 with 10% margins) unless a test fixes them.
 Tolerances as in test_gpu_parity.py: operator 1e-14, basis 1e-12, Gram 1e-10, iterates 1e-10
 for k = 1..5, final true relative residual <= 1e-8.
 """
@@ -38,6 +40,13 @@ def _box(p, **opts):
 
 GRIDS = [("box3d_ragged", (37, 19, 21), 31), ("box2d_ragged", (70, 45), 32), ("box3d_one_slab", (33, 9, 16), 33),
          ("box3d_flat", (5, 1, 3), 34), ("box3d_single", (1, 1, 1), 35), ("box3d_deep", (3, 2, 50), 36)]
+# nx even in 3D: the register-blocked FP64 step and residual. 70 x 13: 35 pairs per row group,
+# so warps straddle row groups and the last warp column is partial; 2 x 9: one pair, both x
+# faces in every lane; 4 x 3 x 70: one partial warp column split over many warps mid-column;
+# 130 x 37 x 35: 65 pairs, ragged row groups (37 = 9 x 4 + 1) and planes.
+EVEN_GRIDS = [("box3d_even_ragged", (70, 13, 11), 37), ("box3d_even_pair", (2, 9, 5), 38),
+              ("box3d_even_deep", (4, 3, 70), 39), ("box3d_even_wide", (130, 37, 35), 40)]
+GRIDS += EVEN_GRIDS
 
 
 def _prob(dims, cfg):
@@ -59,7 +68,10 @@ def test_box_apply_and_residual_match_oracle(name, dims, cfg):
     assert info["rel_res_true"] == pytest.approx(np.linalg.norm(r_true) / np.linalg.norm(p.b), rel=1e-10, abs=1e-14)
 
 
-@pytest.mark.parametrize("name,dims,cfg", GRIDS[:3], ids=[g[0] for g in GRIDS[:3]])
+BASIS_GRIDS = GRIDS[:3] + EVEN_GRIDS
+
+
+@pytest.mark.parametrize("name,dims,cfg", BASIS_GRIDS, ids=[g[0] for g in BASIS_GRIDS])
 @pytest.mark.parametrize("precond", ["jacobi", "none"])
 def test_box_chebyshev_basis_matches_oracle(name, dims, cfg, precond):
     p = _prob(dims, cfg)
@@ -88,7 +100,8 @@ def test_box_gram_solve_matches_oracle(form, s):
     assert _rel(alpha, d0 * O.fgs(Gt0, ct0, 20)) <= 1e-9
 
 
-@pytest.mark.parametrize("dims,cfg,s,nu", [((37, 19, 21), 31, 8, 25), ((70, 45), 32, 4, 20), ((33, 9, 16), 33, 12, 30)])
+@pytest.mark.parametrize("dims,cfg,s,nu", [((37, 19, 21), 31, 8, 25), ((70, 45), 32, 4, 20), ((33, 9, 16), 33, 12, 30),
+                                           ((70, 13, 11), 37, 8, 25), ((130, 37, 35), 40, 6, 20)])
 @pytest.mark.parametrize("form", ["direct", "moments", "fused"])
 def test_box_per_iterate_parity_first_five_outer_iterations(dims, cfg, s, nu, form):
     p = _prob(dims, cfg)
