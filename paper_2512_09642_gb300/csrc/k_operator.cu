@@ -94,8 +94,9 @@ __device__ __forceinline__ void mom_block_store(const MomAcc<double>& m, void* p
     }
 }
 
+template <int NT = BX * BY>
 __device__ __forceinline__ void mom_block_store(const MomAcc<float>& m, void* part, int nblk) {
-    __shared__ float sh[BX * BY / 32][4];
+    __shared__ float sh[NT / 32][4];
     const int t = threadIdx.x + BX * threadIdx.y, lane = t & 31, w = t >> 5;
     float ah = m.ah, al = m.al, bh = m.bh, bl = m.bl;
 #pragma unroll
@@ -112,7 +113,7 @@ __device__ __forceinline__ void mom_block_store(const MomAcc<float>& m, void* pa
     __syncthreads();
     if (w == 0) {
         // the block's warps, lane k holding warp k's pairs: a butterfly over lanes 0..NW-1
-        constexpr int NW = BX * BY / 32;
+        constexpr int NW = NT / 32;
         static_assert(NW >= 2 && NW <= 32 && (NW & (NW - 1)) == 0, "warps per block: a power of 2 up to 32");
         const bool has = lane < NW;
         ah = has ? sh[lane][0] : 0.f;
@@ -753,20 +754,26 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_box_f32_pair(const float* __res
 // waves of resident blocks), the same persistent march over 64-point tiles 0.205 ms.
 constexpr int BOXY = 4;   // rows per thread (even)
 constexpr int BOXW = 4;   // warps per block
+// resident blocks per SM the launch bound asks for: FP64 3 (at most 168 registers), FP32 4
+template <typename T> constexpr int box_reg_min_blocks() { return sizeof(T) == 8 ? 3 : 4; }
 
-// The thread's place in the flattened order for warp column c.
-struct BoxLane {
+// The thread's place in the flattened order for warp column c, with the in-plane offsets of
+// its Y + 2 rows (fixed while it marches the column; a plane only adds k nx ny).
+template <int Y> struct BoxLane {
     int i, jb;                        // first x of the pair, first row
     bool valid;                       // the lane has a pair
     bool lload, rload, lzero, rzero;  // outer neighbours: loaded / 0 (x faces) / from a lane
+    unsigned rows;                    // bit r: row jb - 1 + r lies in the grid (and valid)
+    int roff[Y + 2];                  // nx (jb - 1 + r) + i for those rows, else 0
 };
 
-__device__ __forceinline__ BoxLane box_lane(int64_t c, int nx, int ny, int Y) {
+template <int Y>
+__device__ __forceinline__ BoxLane<Y> box_lane(int64_t c, int nx, int ny) {
     const int lane = threadIdx.x;
     const int np = nx / 2;
     const int64_t nl = (int64_t)np * ((ny + Y - 1) / Y);
     const int64_t L = c * 32 + lane;
-    BoxLane b;
+    BoxLane<Y> b;
     b.valid = L < nl;
     const int xp = b.valid ? (int)(L % np) : 0;
     b.i = 2 * xp;
@@ -775,57 +782,82 @@ __device__ __forceinline__ BoxLane box_lane(int64_t c, int nx, int ny, int Y) {
     b.rzero = xp == np - 1;   // also every lane whose next lane is past the last pair
     b.lload = b.valid && !b.lzero && lane == 0;
     b.rload = b.valid && !b.rzero && lane == 31;
-    return b;
-}
-
-// S(k), the 3 x 3 in-plane sums of plane k at the thread's 2 x Y points (0 outside the grid);
-// c receives the centre pairs of the Y rows.
-template <int Y>
-__device__ __forceinline__ void box_reg_plane(const double* __restrict__ p, int nx, int ny, int nz, int k,
-                                              const BoxLane& b, double one, double2 (&c)[Y], double (&S)[Y][2]) {
-    const bool kv = k >= 0 && k < nz;
-    double2 v[Y + 2];
-    double el[Y + 2], er[Y + 2];
+    b.rows = 0u;
 #pragma unroll
     for (int r = 0; r < Y + 2; ++r) {
         const int jj = b.jb - 1 + r;
-        const bool rv = b.valid && kv && jj >= 0 && jj < ny;
-        const int64_t off = rv ? (int64_t)nx * ny * k + (int64_t)nx * jj + b.i : 0;
-        v[r] = rv ? __ldg(reinterpret_cast<const double2*>(p + off)) : make_double2(0.0, 0.0);
-        el[r] = (rv && b.lload) ? ldg(p + off - 1) : 0.0;
-        er[r] = (rv && b.rload) ? ldg(p + off + 2) : 0.0;
+        const bool rv = b.valid && jj >= 0 && jj < ny;
+        b.rows |= rv ? 1u << r : 0u;
+        b.roff[r] = rv ? nx * jj + b.i : 0;
     }
-    double R[Y + 2][2];
+    return b;
+}
+
+template <typename T> __device__ __forceinline__ typename Pair<T>::type pair_of(T x, T y) { return {x, y}; }
+
+// The thread's rows of plane k (pk = p + k nx ny, kv: 0 <= k < nz): its pair per row, and the
+// edge point lane 0 (x = i - 1) or lane 31 (x = i + 2) loads; 0 outside the grid.
+template <typename T, int Y> struct BoxRows {
+    typename Pair<T>::type v[Y + 2];
+    T e[Y + 2];
+};
+
+template <typename T, int Y>
+__device__ __forceinline__ BoxRows<T, Y> box_reg_load(const T* __restrict__ pk, bool kv, const BoxLane<Y>& b) {
+    const int de = b.lload ? -1 : 2;
+    const bool edge = b.lload || b.rload;
+    BoxRows<T, Y> w;
 #pragma unroll
     for (int r = 0; r < Y + 2; ++r) {
-        double l = __shfl_up_sync(0xffffffffu, v[r].y, 1);
-        double rr = __shfl_down_sync(0xffffffffu, v[r].x, 1);
-        if (b.lload || b.lzero) l = el[r];
-        if (b.rload || b.rzero) rr = er[r];
-        const double m = add1(v[r].x, v[r].y, one);
+        const bool rv = kv && ((b.rows >> r) & 1u);
+        w.v[r] = rv ? __ldg(reinterpret_cast<const typename Pair<T>::type*>(pk + b.roff[r])) : pair_of<T>(T(0), T(0));
+        w.e[r] = (rv && edge) ? ldg(pk + b.roff[r] + de) : T(0);
+    }
+    return w;
+}
+
+// S, the 3 x 3 in-plane sums of the loaded plane at the thread's 2 x Y points; c receives the
+// centre pairs of the Y rows.
+template <typename T, int Y>
+__device__ __forceinline__ void box_reg_sums(const BoxRows<T, Y>& w, const BoxLane<Y>& b, T one,
+                                             typename Pair<T>::type (&c)[Y], T (&S)[Y][2]) {
+    T R[Y + 2][2];
+#pragma unroll
+    for (int r = 0; r < Y + 2; ++r) {
+        T l = __shfl_up_sync(0xffffffffu, w.v[r].y, 1);
+        T rr = __shfl_down_sync(0xffffffffu, w.v[r].x, 1);
+        if (b.lzero) l = T(0);
+        if (b.rzero) rr = T(0);
+        if (b.lload) l = w.e[r];
+        if (b.rload) rr = w.e[r];
+        const T m = add1(w.v[r].x, w.v[r].y, one);
         R[r][0] = add1(l, m, one);
         R[r][1] = add1(m, rr, one);
     }
 #pragma unroll
-    for (int t = 0; t < Y; ++t) c[t] = v[t + 1];
+    for (int t = 0; t < Y; ++t) c[t] = w.v[t + 1];
 #pragma unroll
     for (int x = 0; x < 2; ++x)
 #pragma unroll
         for (int t = 0; t < Y; t += 2) {
-            const double m = add1(R[t + 1][x], R[t + 2][x], one);
+            const T m = add1(R[t + 1][x], R[t + 2][x], one);
             S[t][x] = add1(R[t][x], m, one);
             S[t + 1][x] = add1(m, R[t + 3][x], one);
         }
 }
 
-// The warp's share of the persistent march: calls pre(k, row, i) one plane sum ahead of
-// emit(k, row, i, pc, B, pre value) for each of the thread's points in the grid (pc, B and the
-// pre value as pairs at x = i, i + 1).
-template <int Y, typename Pre, typename Emit>
-__device__ __forceinline__ void box_reg_sweep(const double* __restrict__ p, int nx, int ny, int nz, double one, Pre pre,
-                                              Emit emit) {
+// The warp's share of the persistent march: calls pre(e) ahead of emit(e, pc, B, pre value)
+// for each of the thread's points in the grid, e = the element offset of the pair at x = i
+// (pc, B and the pre value as pairs at x = i, i + 1). PREF: the rows of plane k + 2 and the
+// pre values of plane k + 1 are loaded while plane k's output is formed (the FP32 step, which
+// waits on memory); without it a plane's loads are issued at the top of its iteration (the
+// FP64 kernels, which the FP64 pipe bounds, keep the registers for resident warps instead).
+template <typename T, int Y, bool PREF, typename Pre, typename Emit>
+__device__ __forceinline__ void box_reg_sweep(const T* __restrict__ p, int nx, int ny, int nz, T one, Pre pre, Emit emit) {
     static_assert(Y % 2 == 0, "rows per thread: even");
+    using V = typename Pair<T>::type;
     const int np = nx / 2;
+    const int64_t sxy = (int64_t)nx * ny;
     const int64_t nwc = ((int64_t)np * ((ny + Y - 1) / Y) + 31) / 32;   // warp columns
     const int64_t U = nwc * nz;
     const int64_t nw = (int64_t)gridDim.x * BOXW, w = (int64_t)blockIdx.x * BOXW + threadIdx.y;
@@ -835,11 +867,17 @@ __device__ __forceinline__ void box_reg_sweep(const double* __restrict__ p, int 
         const int64_t c = u / nz;
         const int k0 = (int)(u - c * nz);
         const int k1 = (int)(k0 + (u1 - u) < (int64_t)nz ? k0 + (u1 - u) : (int64_t)nz);
-        const BoxLane b = box_lane(c, nx, ny, Y);
-        double A0[Y][2], A1[Y][2], S[Y][2];   // A0: S(k-1) + S(k), A1: S(k)
-        double2 pc[Y], pn[Y];
-        box_reg_plane<Y>(p, nx, ny, nz, k0 - 1, b, one, pn, A0);
-        box_reg_plane<Y>(p, nx, ny, nz, k0, b, one, pc, S);
+        const BoxLane<Y> b = box_lane<Y>(c, nx, ny);
+        auto plane = [&](int k) { return box_reg_load<T, Y>(p + sxy * k, k >= 0 && k < nz, b); };
+        auto pre_rows = [&](int k, V (&ev)[Y]) {
+#pragma unroll
+            for (int t = 0; t < Y; ++t)
+                ev[t] = (k < k1 && ((b.rows >> (t + 1)) & 1u)) ? pre(sxy * k + b.roff[t + 1]) : pair_of<T>(T(0), T(0));
+        };
+        T A0[Y][2], A1[Y][2], S[Y][2];   // A0: S(k-1) + S(k), A1: S(k)
+        V pc[Y], pn[Y];
+        box_reg_sums<T, Y>(plane(k0 - 1), b, one, pn, A0);
+        box_reg_sums<T, Y>(plane(k0), b, one, pc, S);
 #pragma unroll
         for (int t = 0; t < Y; ++t)
 #pragma unroll
@@ -847,16 +885,30 @@ __device__ __forceinline__ void box_reg_sweep(const double* __restrict__ p, int 
                 A0[t][x] = add1(A0[t][x], S[t][x], one);
                 A1[t][x] = S[t][x];
             }
+        BoxRows<T, Y> nxt;
+        V evn[Y];
+        if (PREF) {
+            nxt = plane(k0 + 1);
+            pre_rows(k0, evn);
+        }
         for (int k = k0; k < k1; ++k) {
-            double2 ev[Y];
+            V ev[Y];
+            BoxRows<T, Y> cur;
+            if (PREF) {
 #pragma unroll
-            for (int t = 0; t < Y; ++t)
-                ev[t] = (b.valid && b.jb + t < ny) ? pre(k, b.jb + t, b.i) : make_double2(0.0, 0.0);
-            box_reg_plane<Y>(p, nx, ny, nz, k + 1, b, one, pn, S);
+                for (int t = 0; t < Y; ++t) ev[t] = evn[t];
+                cur = nxt;
+                nxt = plane(k + 2 <= k1 ? k + 2 : nz);   // plane nz: zeros, nothing loaded
+                pre_rows(k + 1, evn);
+            } else {
+                pre_rows(k, ev);
+                cur = plane(k + 1);
+            }
+            box_reg_sums<T, Y>(cur, b, one, pn, S);
 #pragma unroll
             for (int t = 0; t < Y; ++t) {
-                const double2 B = make_double2(add1(A0[t][0], S[t][0], one), add1(A0[t][1], S[t][1], one));
-                if (b.valid && b.jb + t < ny) emit(k, b.jb + t, b.i, pc[t], B, ev[t]);
+                const V B = pair_of<T>(add1(A0[t][0], S[t][0], one), add1(A0[t][1], S[t][1], one));
+                if ((b.rows >> (t + 1)) & 1u) emit(sxy * k + b.roff[t + 1], pc[t], B, ev[t]);
 #pragma unroll
                 for (int x = 0; x < 2; ++x) {
                     A0[t][x] = add1(A1[t][x], S[t][x], one);
@@ -869,26 +921,21 @@ __device__ __forceinline__ void box_reg_sweep(const double* __restrict__ p, int 
     }
 }
 
-template <int Y, bool FIRST, bool GRAM>
-__global__ void __launch_bounds__(32 * BOXW, 3) k_cheb_box_reg(const double* __restrict__ p,
-                                                               const double* __restrict__ q, double* __restrict__ out,
-                                                               int nx, int ny, int nz, double ca, double cb,
-                                                               const Ctl* __restrict__ ctl, double one, void* mom,
-                                                               int nblk) {
+template <typename T, int Y, bool FIRST, bool GRAM>
+__global__ void __launch_bounds__(32 * BOXW, box_reg_min_blocks<T>()) k_cheb_box_reg(
+    const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ out, int nx, int ny, int nz, T ca, T cb,
+    const Ctl* __restrict__ ctl, T one, void* mom, int nblk) {
+    using V = typename Pair<T>::type;
     if (ctl->done) return;
-    const int64_t sxy = (int64_t)nx * ny;
-    MomAcc<double> acc;
-    box_reg_sweep<Y>(
+    MomAcc<T> acc;
+    box_reg_sweep<T, Y, sizeof(T) == 4>(
         p, nx, ny, nz, one,
-        [&](int k, int j, int i) {
-            return FIRST ? make_double2(0.0, 0.0)
-                         : __ldg(reinterpret_cast<const double2*>(q + sxy * k + (int64_t)nx * j + i));
-        },
-        [&](int k, int j, int i, double2 pc, double2 B, double2 qv) {
-            double2 o;
+        [&](int64_t e) { return FIRST ? pair_of<T>(T(0), T(0)) : __ldg(reinterpret_cast<const V*>(q + e)); },
+        [&](int64_t e, V pc, V B, V qv) {
+            V o;
             o.x = FIRST ? fma(cb, B.x, ca * pc.x) : fma(cb, B.x, fma(ca, pc.x, -qv.x));
             o.y = FIRST ? fma(cb, B.y, ca * pc.y) : fma(cb, B.y, fma(ca, pc.y, -qv.y));
-            *reinterpret_cast<double2*>(out + sxy * k + (int64_t)nx * j + i) = o;
+            *reinterpret_cast<V*>(out + e) = o;
             if (GRAM) {
                 acc.add(pc.x, o.x);
                 acc.add(pc.y, o.y);
@@ -938,7 +985,7 @@ __global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restric
 
 // r = b - A x with ||r||^2 on the register-blocked persistent march of k_cheb_box_reg (3D, nx
 // even, b, x and r 16-byte and r32 8-byte aligned); residual modes as k_residual_stencil.
-__global__ void __launch_bounds__(32 * BOXW, 3) k_residual_box_reg(const double* __restrict__ b,
+__global__ void __launch_bounds__(32 * BOXW, box_reg_min_blocks<double>()) k_residual_box_reg(const double* __restrict__ b,
                                                                    const double* __restrict__ x,
                                                                    double* __restrict__ r, float* __restrict__ r32,
                                                                    int nx, int ny, int nz, double* partials, Ctl* ctl,
@@ -949,13 +996,10 @@ __global__ void __launch_bounds__(32 * BOXW, 3) k_residual_box_reg(const double*
         frexp(ctl->scale_next, &kscale);
         kscale -= 1;
     }
-    const int64_t sxy = (int64_t)nx * ny;
     double ss = 0.0;
-    box_reg_sweep<BOXY>(
-        x, nx, ny, nz, one,
-        [&](int k, int j, int i) { return __ldg(reinterpret_cast<const double2*>(b + sxy * k + (int64_t)nx * j + i)); },
-        [&](int k, int j, int i, double2 pc, double2 B, double2 bv) {
-            const int64_t e = sxy * k + (int64_t)nx * j + i;
+    box_reg_sweep<double, BOXY, false>(
+        x, nx, ny, nz, one, [&](int64_t e) { return __ldg(reinterpret_cast<const double2*>(b + e)); },
+        [&](int64_t e, double2 pc, double2 B, double2 bv) {
             const double r0 = fma(fma(27.0, pc.x, -B.x), -one, bv.x);   // bv - (27 pc - B)
             const double r1 = fma(fma(27.0, pc.y, -B.y), -one, bv.y);
             if (r) *reinterpret_cast<double2*>(r + e) = make_double2(r0, r1);
@@ -998,6 +1042,7 @@ dim3 box_pair_grid(const OpDesc& op) {
 // FP64 register-blocked box step: 3D, nx even and 16-byte aligned vectors. The grid is the
 // blocks resident at once (the fewest over the step's instantiations), at most one warp per
 // (warp column, plane) unit.
+template <typename T>
 int box_reg_per_sm() {
     static int per_sm[64] = {0};
     int dev = 0;
@@ -1005,23 +1050,29 @@ int box_reg_per_sm() {
     if (!per_sm[dev]) {
         int m = 1 << 30, b = 0;
         const int nt = 32 * BOXW;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<BOXY, true, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<BOXY, false, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<BOXY, true, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<BOXY, false, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<T, BOXY, true, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<T, BOXY, false, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<T, BOXY, true, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<T, BOXY, false, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
         per_sm[dev] = (m >= 1 && m < (1 << 30)) ? m : 1;
     }
     return per_sm[dev];
 }
+template <typename T>
 dim3 box_reg_grid(const OpDesc& op) {
     const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + BOXY - 1) / BOXY) + 31) / 32;
     const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
-    const int64_t cap = (int64_t)box_reg_per_sm() * device_sm_count();
+    const int64_t cap = (int64_t)box_reg_per_sm<T>() * device_sm_count();
     return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
 }
-bool box_reg_ok(const OpDesc& op, const double* p, const double* q, const double* out) {
-    return op.dim == 3 && op.nx % 2 == 0 && ((uintptr_t)p % 16 == 0) && ((uintptr_t)out % 16 == 0) &&
-           (!q || (uintptr_t)q % 16 == 0);
+// the grids the register-blocked box kernels take: 3D, nx even, a plane within 32-bit offsets
+bool box_reg_shape(const OpDesc& op) {
+    return op.dim == 3 && op.nx % 2 == 0 && (int64_t)op.nx * op.ny < (int64_t)INT32_MAX;
+}
+template <typename T>
+bool box_reg_ok(const OpDesc& op, const T* p, const T* q, const T* out) {
+    const size_t al = 2 * sizeof(T);
+    return box_reg_shape(op) && ((uintptr_t)p % al == 0) && ((uintptr_t)out % al == 0) && (!q || (uintptr_t)q % al == 0);
 }
 int box_res_reg_per_sm() {
     static int per_sm[64] = {0};
@@ -1040,7 +1091,7 @@ dim3 box_res_reg_grid(const OpDesc& op) {
     return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
 }
 bool box_res_reg_ok(const OpDesc& op, const double* b, const double* x, const double* r, const float* r32) {
-    return op.dim == 3 && op.nx % 2 == 0 && ((uintptr_t)b % 16 == 0) && ((uintptr_t)x % 16 == 0) &&
+    return box_reg_shape(op) && ((uintptr_t)b % 16 == 0) && ((uintptr_t)x % 16 == 0) &&
            (!r || (uintptr_t)r % 16 == 0) && (!r32 || (uintptr_t)r32 % 8 == 0);
 }
 bool box_pair_ok(const OpDesc& op, const float* p, const float* q, const float* out) {
@@ -1148,8 +1199,8 @@ int cheb_step_blocks(const OpDesc& op, bool fp32) {
     const int kz = fp32 ? kz_step<float>() : kz_step<double>();
     dim3 g;
     if (op.box) {
-        if (fp32) g = op.nx % 2 == 0 ? box_pair_grid(op) : box_grid(op);
-        else g = op.dim == 3 && op.nx % 2 == 0 ? box_reg_grid(op) : box_grid(op);
+        if (box_reg_shape(op)) g = fp32 ? box_reg_grid<float>(op) : box_reg_grid<double>(op);
+        else g = fp32 && op.nx % 2 == 0 ? box_pair_grid(op) : box_grid(op);
     }
     else if (op.wx == nullptr && op.nx % 2 == 0) g = pair_grid(op, kz);
     else g = stencil_grid(op, kz);
@@ -1163,11 +1214,9 @@ cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, d
         // the fused moments need a stencil operator and the block count cheb_step_blocks reports
         if (op.kind != OP_STENCIL) return cudaErrorInvalidValue;
         if (!op.box && op.wx == nullptr && op.nx % 2 == 0 && !use_pair(op, p, q, out)) return cudaErrorInvalidValue;
-        if (op.box && std::is_same<T, float>::value && op.nx % 2 == 0 &&
+        if (op.box && box_reg_shape(op) && !box_reg_ok<T>(op, p, q, out)) return cudaErrorInvalidValue;
+        if (op.box && !box_reg_shape(op) && std::is_same<T, float>::value && op.nx % 2 == 0 &&
             !box_pair_ok(op, (const float*)p, (const float*)q, (const float*)out))
-            return cudaErrorInvalidValue;
-        if (op.box && std::is_same<T, double>::value && op.dim == 3 && op.nx % 2 == 0 &&
-            !box_reg_ok(op, (const double*)p, (const double*)q, (const double*)out))
             return cudaErrorInvalidValue;
     }
     if (op.kind == OP_STENCIL && op.box) {
@@ -1177,6 +1226,13 @@ cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, d
         const double D = op.dim == 3 ? 26.0 : 8.0;
         const T ca = (T)(jacobi ? c * (1.0 - sigma) + c / D : c * (D + 1.0 - sigma));
         const T cb = (T)(jacobi ? -c / D : -c);
+        if (box_reg_ok<T>(op, p, q, out)) {
+            const dim3 g3 = box_reg_grid<T>(op), block(32, BOXW);
+#define ARGS p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl, T(1)
+            SSTEP_STEP_LAUNCH(k_cheb_box_reg, g3, T, BOXY);
+#undef ARGS
+            return cudaGetLastError();
+        }
         const dim3 grid = box_grid(op), block(BX, BY);
         if (std::is_same<T, float>::value) {
             const float* pf = (const float*)p;
@@ -1194,15 +1250,6 @@ cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, d
             }
 #undef ARGS
             return cudaGetLastError();
-        }
-        if constexpr (std::is_same<T, double>::value) {
-            if (box_reg_ok(op, p, q, out)) {
-                const dim3 g3 = box_reg_grid(op), block(32, BOXW);
-#define ARGS p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl, 1.0
-                SSTEP_STEP_LAUNCH(k_cheb_box_reg, g3, BOXY);
-#undef ARGS
-                return cudaGetLastError();
-            }
         }
 #define ARGS p, q, out, op.nx, op.ny, op.nz, ca, cb, ctl, T(1)
         if (op.dim == 3) SSTEP_STEP_LAUNCH(k_cheb_box, grid, T, 3);
@@ -1246,7 +1293,7 @@ size_t residual_partials_needed(const OpDesc& op) {
         // either kernel may run (the register-blocked one needs aligned vectors)
         const dim3 g = box_grid(op);
         const size_t n1 = (size_t)g.x * g.y * g.z;
-        if (op.dim != 3 || op.nx % 2 != 0) return n1;
+        if (!box_reg_shape(op)) return n1;
         return std::max(n1, (size_t)box_res_reg_grid(op).x);
     }
     if (op.kind == OP_STENCIL) {
