@@ -944,6 +944,91 @@ __global__ void __launch_bounds__(32 * BOXW, box_reg_min_blocks<T>()) k_cheb_box
     if (GRAM) mom_block_store<32 * BOXW>(acc, mom, nblk);
 }
 
+// FP64 7-point Poisson step (3D, nx even, 16-byte aligned vectors) on the same register-blocked
+// persistent march: a thread owns an x pair in STARY rows of a warp column and loads its
+// STARY + 2 rows of a plane once; the y neighbours of its rows come from its own registers,
+// the z neighbours from the previous and next plane's rows it holds, the x neighbours from
+// the adjacent lanes. 5 load instructions per 4 points and plane (with the edge loads of
+// lanes 0 and 31 and q) against 12 for the pair kernel, whose loads filled the L1 queue
+// (stall tex_throttle 35 per issue at 192^3) with the FP64 pipe 81% busy. Same sums in the
+// same order as k_cheb_poisson_pair (bitwise equal outputs). Measured at 256^3: 0.2315 ->
+// 0.205 ms per step, 0.81 -> 0.91 of the FP64 FMA rate. The FP32 step keeps the pair kernel
+// (0.80 of HBM; this form measured 0.61).
+constexpr int STARY = 2;   // rows per thread
+
+template <bool FIRST, bool GRAM>
+__global__ void __launch_bounds__(32 * BOXW, 4) k_cheb_star_reg(const double* __restrict__ p,
+                                                                const double* __restrict__ q, double* __restrict__ out,
+                                                                int nx, int ny, int nz, double c1, double c2,
+                                                                const Ctl* __restrict__ ctl, double one, void* mom,
+                                                                int nblk) {
+    constexpr int Y = STARY;
+    using V = double2;
+    if (ctl->done) return;
+    const int np = nx / 2;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int64_t nwc = ((int64_t)np * ((ny + Y - 1) / Y) + 31) / 32;   // warp columns
+    const int64_t U = nwc * nz;
+    const int64_t nw = (int64_t)gridDim.x * BOXW, w = (int64_t)blockIdx.x * BOXW + threadIdx.y;
+    int64_t u = U * w / nw;
+    const int64_t u1 = U * (w + 1) / nw;
+    MomAcc<double> acc;
+    while (u < u1) {
+        const int64_t c = u / nz;
+        const int k0 = (int)(u - c * nz);
+        const int k1 = (int)(k0 + (u1 - u) < (int64_t)nz ? k0 + (u1 - u) : (int64_t)nz);
+        const BoxLane<Y> b = box_lane<Y>(c, nx, ny);
+        auto plane = [&](int k) { return box_reg_load<double, Y>(p + sxy * k, k >= 0 && k < nz, b); };
+        V pd[Y];   // the rows of plane k - 1
+        {
+            const BoxRows<double, Y> w0 = plane(k0 - 1);
+#pragma unroll
+            for (int t = 0; t < Y; ++t) pd[t] = w0.v[t + 1];
+        }
+        BoxRows<double, Y> cur = plane(k0);
+        for (int k = k0; k < k1; ++k) {
+            V qv[Y];
+#pragma unroll
+            for (int t = 0; t < Y; ++t)
+                qv[t] = (!FIRST && ((b.rows >> (t + 1)) & 1u))
+                            ? __ldg(reinterpret_cast<const V*>(q + sxy * k + b.roff[t + 1]))
+                            : make_double2(0.0, 0.0);
+            const BoxRows<double, Y> up = plane(k + 1);
+#pragma unroll
+            for (int t = 0; t < Y; ++t) {
+                const V pc = cur.v[t + 1];
+                // left of the pair: the lane below's right point; right: the lane above's left
+                // point; from memory at the warp's edges, 0 at the grid's x faces
+                double xl = __shfl_up_sync(0xffffffffu, pc.y, 1);
+                double xr = __shfl_down_sync(0xffffffffu, pc.x, 1);
+                if (b.lzero) xl = 0.0;
+                if (b.rzero) xr = 0.0;
+                if (b.lload) xl = cur.e[t + 1];
+                if (b.rload) xr = cur.e[t + 1];
+                const V ym = cur.v[t], yp = cur.v[t + 2], pup = up.v[t + 1], pdn = pd[t];
+                double s0 = add1(add1(xl, pc.y, one), add1(ym.x, yp.x, one), one);
+                double s1 = add1(add1(pc.x, xr, one), add1(ym.y, yp.y, one), one);
+                s0 = add1(s0, add1(pdn.x, pup.x, one), one);
+                s1 = add1(s1, add1(pdn.y, pup.y, one), one);
+                V o;
+                o.x = FIRST ? fma(c2, s0, c1 * pc.x) : fma(c2, s0, fma(c1, pc.x, -qv[t].x));
+                o.y = FIRST ? fma(c2, s1, c1 * pc.y) : fma(c2, s1, fma(c1, pc.y, -qv[t].y));
+                if ((b.rows >> (t + 1)) & 1u) {
+                    *reinterpret_cast<V*>(out + sxy * k + b.roff[t + 1]) = o;
+                    if (GRAM) {
+                        acc.add(pc.x, o.x);
+                        acc.add(pc.y, o.y);
+                    }
+                }
+                pd[t] = pc;
+            }
+            cur = up;
+        }
+        u += k1 - k0;
+    }
+    if (GRAM) mom_block_store<32 * BOXW>(acc, mom, nblk);
+}
+
 // r = b - A x = b - (3^d x - B) with ||r||^2 (residual modes as k_residual_stencil).
 template <int DIM>
 __global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restrict__ b, const double* __restrict__ x,
@@ -1074,6 +1159,30 @@ bool box_reg_ok(const OpDesc& op, const T* p, const T* q, const T* out) {
     const size_t al = 2 * sizeof(T);
     return box_reg_shape(op) && ((uintptr_t)p % al == 0) && ((uintptr_t)out % al == 0) && (!q || (uintptr_t)q % al == 0);
 }
+// FP64 register-blocked 7-point step: the shapes of the box kernels, Poisson weights
+int star_reg_per_sm() {
+    static int per_sm[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!per_sm[dev]) {
+        int m = 1 << 30, b = 0;
+        const int nt = 32 * BOXW;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_star_reg<true, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_star_reg<false, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_star_reg<true, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_star_reg<false, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
+        per_sm[dev] = (m >= 1 && m < (1 << 30)) ? m : 1;
+    }
+    return per_sm[dev];
+}
+dim3 star_reg_grid(const OpDesc& op) {
+    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + STARY - 1) / STARY) + 31) / 32;
+    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
+    const int64_t cap = (int64_t)star_reg_per_sm() * device_sm_count();
+    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
+}
+bool star_reg_shape(const OpDesc& op) { return !op.box && op.wx == nullptr && box_reg_shape(op); }
+
 int box_res_reg_per_sm() {
     static int per_sm[64] = {0};
     int dev = 0;
@@ -1166,6 +1275,21 @@ void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, dou
         const double d2 = 2.0 * op.dim;
         const T c1 = (T)(jacobi ? c * (1.0 - sigma) : c * (d2 - sigma));
         const T c2 = (T)(jacobi ? -c / d2 : -c);
+        if constexpr (std::is_same<T, double>::value) {
+            if (DIM == 3 && star_reg_shape(op) && use_pair(op, p, q, out)) {
+                const dim3 g3 = star_reg_grid(op), block(32, BOXW);
+#define ARGS p, q, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.0
+                if (first) {
+                    if (mom) k_cheb_star_reg<true, true><<<g3, block, 0, st>>>(ARGS, mom, (int)g3.x);
+                    else k_cheb_star_reg<true, false><<<g3, block, 0, st>>>(ARGS, nullptr, (int)g3.x);
+                } else {
+                    if (mom) k_cheb_star_reg<false, true><<<g3, block, 0, st>>>(ARGS, mom, (int)g3.x);
+                    else k_cheb_star_reg<false, false><<<g3, block, 0, st>>>(ARGS, nullptr, (int)g3.x);
+                }
+#undef ARGS
+                return;
+            }
+        }
         if (use_pair(op, p, q, out)) {
             const dim3 g2 = pair_grid(op, kz_step<T>());
 #define ARGS p, q, out, op.nx, op.ny, op.nz, c1, c2, ctl, T(1)
@@ -1202,6 +1326,7 @@ int cheb_step_blocks(const OpDesc& op, bool fp32) {
         if (box_reg_shape(op)) g = fp32 ? box_reg_grid<float>(op) : box_reg_grid<double>(op);
         else g = fp32 && op.nx % 2 == 0 ? box_pair_grid(op) : box_grid(op);
     }
+    else if (!fp32 && star_reg_shape(op)) g = star_reg_grid(op);
     else if (op.wx == nullptr && op.nx % 2 == 0) g = pair_grid(op, kz);
     else g = stencil_grid(op, kz);
     return (int)(g.x * g.y * g.z);

@@ -45,9 +45,16 @@ CASES = [
     ("diffusion2d_stencil", lambda: W.make("d2", (45, 33), kappa_sigma=1.0, config=13), "stencil"),
     ("diffusion3d_stencil", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), "stencil"),
     ("diffusion3d_csr", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), "csr"),
-    # even nx: the two-points-per-thread Poisson kernels (ragged in every direction)
+    # even nx: the two-points-per-thread Poisson kernels (ragged in every direction); in 3D the
+    # FP64 step's register-blocked persistent march (warp columns of 32 lanes over (row pair,
+    # x pair): 70 x 13 straddles row pairs and leaves a partial last column; 2 x 9 is one pair
+    # with both x faces; 4 x 3 x 70 splits one column over many warps mid-column; 130 x 37 x 35
+    # has 65 pairs, an odd ny and ragged planes)
     ("poisson3d_even_ragged", lambda: W.make("p3e", (70, 13, 11), config=17), "stencil"),
     ("poisson2d_even_ragged", lambda: W.make("p2e", (130, 33), config=18), "stencil"),
+    ("poisson3d_even_pair", lambda: W.make("p3e", (2, 9, 5), config=19), "stencil"),
+    ("poisson3d_even_deep", lambda: W.make("p3e", (4, 3, 70), config=20), "stencil"),
+    ("poisson3d_even_wide", lambda: W.make("p3e", (130, 37, 35), config=21), "stencil"),
 ]
 
 
@@ -122,6 +129,7 @@ SOLVE_CASES = [
     ("diffusion3d_ragged_s12", lambda: W.make("d3", (21, 17, 9), kappa_sigma=1.0, config=14), "stencil", 12, 30),
     ("diffusion2d_csr_s8", lambda: W.make("d2", (45, 33), kappa_sigma=0.5, config=13), "csr", 8, 20),
     ("poisson3d_even_ragged_s8", lambda: W.make("p3e", (70, 13, 11), config=17), "stencil", 8, 25),
+    ("poisson3d_even_wide_s8", lambda: W.make("p3e", (130, 37, 35), config=21), "stencil", 8, 25),
 ]
 
 
@@ -131,13 +139,14 @@ FUSED_CASES = [
     ("config1_poisson2d_64_stencil", W.poisson2d_64, "stencil", 4, 20),
     ("poisson3d_32_stencil_s8", lambda: W.poisson3d(32), "stencil", 8, 25),
     ("poisson3d_even_ragged_s8", lambda: W.make("p3e", (70, 13, 11), config=17), "stencil", 8, 25),
+    ("poisson3d_even_wide_s8", lambda: W.make("p3e", (130, 37, 35), config=21), "stencil", 8, 25),
     ("poisson3d_odd_ragged_s12", lambda: W.make("p3", (19, 13, 11), config=12), "stencil", 12, 30),
     ("poisson2d_odd_s1", lambda: W.make("p2", (37, 29), config=11), "stencil", 1, 5),
 ]
 
 
-@pytest.mark.parametrize("name,make,mode,s,nu", SOLVE_CASES + FUSED_CASES[3:],
-                         ids=[c[0] for c in SOLVE_CASES + FUSED_CASES[3:]])
+@pytest.mark.parametrize("name,make,mode,s,nu", SOLVE_CASES + FUSED_CASES[4:],
+                         ids=[c[0] for c in SOLVE_CASES + FUSED_CASES[4:]])
 @pytest.mark.parametrize("form", ["direct", "moments", "fused"])
 def test_per_iterate_parity_first_five_outer_iterations(name, make, mode, s, nu, form):
     """x_k and r_k, k = 1..5, within 1e-10 of the oracle (which forms G = P^T A P directly)
