@@ -948,12 +948,13 @@ __global__ void __launch_bounds__(32 * BOXW, box_reg_min_blocks<T>()) k_cheb_box
 // persistent march: a thread owns an x pair in STARY rows of a warp column and loads its
 // STARY + 2 rows of a plane once; the y neighbours of its rows come from its own registers,
 // the z neighbours from the previous and next plane's rows it holds, the x neighbours from
-// the adjacent lanes. 5 load instructions per 4 points and plane (with the edge loads of
-// lanes 0 and 31 and q) against 12 for the pair kernel, whose loads filled the L1 queue
-// (stall tex_throttle 35 per issue at 192^3) with the FP64 pipe 81% busy. Same sums in the
+// the adjacent lanes: 10 load instructions and 96 B through L1 per 4 points and plane (its
+// 4 rows, their edge loads in lanes 0 and 31, q) against 12 and 128 B for the pair kernel,
+// whose loads filled the L1 queue (stall tex_throttle 35 per issue at 192^3) with the FP64
+// pipe 81% busy; with a quarter of the resident warps the pipe is 91% busy. Same sums in the
 // same order as k_cheb_poisson_pair (bitwise equal outputs). Measured at 256^3: 0.2315 ->
-// 0.205 ms per step, 0.81 -> 0.91 of the FP64 FMA rate. The FP32 step keeps the pair kernel
-// (0.80 of HBM; this form measured 0.61).
+// 0.205 ms per step (0.81 -> 0.91 of the FP64 FMA rate). The FP32 step keeps the pair
+// kernel (0.80 of HBM; this form measured 0.61).
 constexpr int STARY = 2;   // rows per thread
 
 template <bool FIRST, bool GRAM>
