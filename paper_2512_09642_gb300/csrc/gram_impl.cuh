@@ -251,27 +251,28 @@ struct GramParams {
 // nu forward Gauss-Seidel sweeps on one right-hand side, lane j owning row j (lanes >= S and
 // rows whose bit is clear in `kept` hold 0): grow = row `lane` of the scaled matrix divided by
 // its diagonal, chat = the scaled right-hand side over the same diagonal. A sweep is S
-// warp-wide steps: step i broadcasts the new a_i; rows below i take its product into this
-// sweep's accumulator u (new values, lower triangle), rows above into the next sweep's v
-// (old values, upper triangle). Returns a_lane.
+// warp-wide steps: step i broadcasts a_i = w_i and every other row takes its product into its
+// accumulator w, which row i then restarts at chat; so when step j reads it, w_j = chat_j -
+// sum_(i > j) G^_ji a_i (previous sweep) - sum_(i < j) G^_ji a_i (this sweep), the terms in
+// the order of i. The dropped rows and columns are zeroed once up front (their a_i stay 0),
+// so a step's dependent chain is one shuffle, one FMA and one select. Returns a_lane.
 template <int S>
-__device__ __forceinline__ double fgs_lane(const double (&grow)[S], double chat, unsigned kept, int nu) {
+__device__ __forceinline__ double fgs_lane(const double (&grow_in)[S], double chat, unsigned kept, int nu) {
     const int lane = threadIdx.x & 31;
-    double a = 0.0;
-    double u = chat, v = chat;
+    const bool kj = lane < S && ((kept >> lane) & 1u);
+    double grow[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) grow[i] = (kj && ((kept >> i) & 1u)) ? grow_in[i] : 0.0;
+    if (!kj) chat = 0.0;
+    double a = 0.0, w = chat;
     for (int sweep = 0; sweep < nu; ++sweep) {
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            double ai = __shfl_sync(0xffffffffu, u, i);
-            if (!((kept >> i) & 1u)) ai = 0.0;
+            const double ai = __shfl_sync(0xffffffffu, w, i);
+            const double wn = fma(-grow[i], ai, w);
             if (lane == i) a = ai;
-            double w = lane > i ? u : v;
-            w = fma(-grow[i], ai, w);
-            if (lane > i) u = w;
-            else if (lane < i) v = w;
+            w = lane == i ? chat : wn;
         }
-        u = v;
-        v = chat;
     }
     return a;
 }
