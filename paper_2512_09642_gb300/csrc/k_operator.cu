@@ -1030,6 +1030,89 @@ __global__ void __launch_bounds__(32 * BOXW, 4) k_cheb_star_reg(const double* __
     if (GRAM) mom_block_store<32 * BOXW>(acc, mom, nblk);
 }
 
+// r = b - A x with ||r||^2 for the 7-point Poisson operator (FP64; 3D, nx even, b, x and r
+// 16-byte and r32 8-byte aligned) on the march of k_cheb_star_reg; residual modes as
+// k_residual_stencil, the neighbour sum in the same order (x-, x+, y-, y+, z-, z+; a missing
+// neighbour adds 0). The mixed forms' FP64 refresh.
+__global__ void __launch_bounds__(32 * BOXW, 4) k_residual_star_reg(const double* __restrict__ b,
+                                                                    const double* __restrict__ x,
+                                                                    double* __restrict__ r, float* __restrict__ r32,
+                                                                    int nx, int ny, int nz, double d2,
+                                                                    double* partials, Ctl* ctl, int mode,
+                                                                    double one) {
+    constexpr int Y = STARY;
+    using V = double2;
+    if (mode == 2 && ctl->done) return;
+    int kscale = 0;   // scale_next = 2^kscale
+    if (mode == 2) {
+        frexp(ctl->scale_next, &kscale);
+        kscale -= 1;
+    }
+    const int np = nx / 2;
+    const int64_t sxy = (int64_t)nx * ny;
+    const int64_t nwc = ((int64_t)np * ((ny + Y - 1) / Y) + 31) / 32;   // warp columns
+    const int64_t U = nwc * nz;
+    const int64_t nw = (int64_t)gridDim.x * BOXW, w = (int64_t)blockIdx.x * BOXW + threadIdx.y;
+    int64_t u = U * w / nw;
+    const int64_t u1 = U * (w + 1) / nw;
+    double ss = 0.0;
+    while (u < u1) {
+        const int64_t c = u / nz;
+        const int k0 = (int)(u - c * nz);
+        const int k1 = (int)(k0 + (u1 - u) < (int64_t)nz ? k0 + (u1 - u) : (int64_t)nz);
+        const BoxLane<Y> bl = box_lane<Y>(c, nx, ny);
+        auto plane = [&](int k) { return box_reg_load<double, Y>(x + sxy * k, k >= 0 && k < nz, bl); };
+        V pd[Y];   // the rows of plane k - 1
+        {
+            const BoxRows<double, Y> w0 = plane(k0 - 1);
+#pragma unroll
+            for (int t = 0; t < Y; ++t) pd[t] = w0.v[t + 1];
+        }
+        BoxRows<double, Y> cur = plane(k0);
+        for (int k = k0; k < k1; ++k) {
+            V bv[Y];
+#pragma unroll
+            for (int t = 0; t < Y; ++t)
+                bv[t] = ((bl.rows >> (t + 1)) & 1u) ? __ldg(reinterpret_cast<const V*>(b + sxy * k + bl.roff[t + 1]))
+                                                    : make_double2(0.0, 0.0);
+            const BoxRows<double, Y> up = plane(k + 1);
+#pragma unroll
+            for (int t = 0; t < Y; ++t) {
+                const V pc = cur.v[t + 1];
+                double xl = __shfl_up_sync(0xffffffffu, pc.y, 1);
+                double xr = __shfl_down_sync(0xffffffffu, pc.x, 1);
+                if (bl.lzero) xl = 0.0;
+                if (bl.rzero) xr = 0.0;
+                if (bl.lload) xl = cur.e[t + 1];
+                if (bl.rload) xr = cur.e[t + 1];
+                const V ym = cur.v[t], yp = cur.v[t + 2], pup = up.v[t + 1], pdn = pd[t];
+                double s0 = add1(add1(add1(add1(add1(xl, pc.y, one), ym.x, one), yp.x, one), pdn.x, one), pup.x, one);
+                double s1 = add1(add1(add1(add1(add1(pc.x, xr, one), ym.y, one), yp.y, one), pdn.y, one), pup.y, one);
+                const double r0 = fma(fma(d2, pc.x, -s0), -one, bv[t].x);   // b - A x
+                const double r1 = fma(fma(d2, pc.y, -s1), -one, bv[t].y);
+                if ((bl.rows >> (t + 1)) & 1u) {
+                    const int64_t e = sxy * k + bl.roff[t + 1];
+                    if (r) *reinterpret_cast<V*>(r + e) = make_double2(r0, r1);
+                    if (r32) *reinterpret_cast<float2*>(r32 + e) = make_float2(d2f_scaled(r0, kscale), d2f_scaled(r1, kscale));
+                    ss = fma(r0, r0, ss);
+                    ss = fma(r1, r1, ss);
+                }
+                pd[t] = pc;
+            }
+            cur = up;
+        }
+        u += k1 - k0;
+    }
+    __shared__ double sh[BOXW];
+    const double v = warp_sum(ss);
+    if (threadIdx.x == 0) sh[threadIdx.y] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int k = 0; k < BOXW; ++k) tot += sh[k];
+    last_block_finish(tot, partials, &ctl->counter2, ctl, mode, (int64_t)nx * ny * nz, (int)gridDim.x);
+}
+
 // r = b - A x = b - (3^d x - B) with ||r||^2 (residual modes as k_residual_stencil).
 template <int DIM>
 __global__ void __launch_bounds__(BX* BY) k_residual_box(const double* __restrict__ b, const double* __restrict__ x,
@@ -1183,6 +1266,23 @@ dim3 star_reg_grid(const OpDesc& op) {
     return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
 }
 bool star_reg_shape(const OpDesc& op) { return !op.box && op.wx == nullptr && box_reg_shape(op); }
+
+int star_res_per_sm() {
+    static int per_sm[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!per_sm[dev]) {
+        int b = 0;
+        per_sm[dev] = (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_residual_star_reg, 32 * BOXW, 0) == cudaSuccess && b >= 1) ? b : 1;
+    }
+    return per_sm[dev];
+}
+dim3 star_res_grid(const OpDesc& op) {
+    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + STARY - 1) / STARY) + 31) / 32;
+    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
+    const int64_t cap = (int64_t)star_res_per_sm() * device_sm_count();
+    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
+}
 
 int box_res_reg_per_sm() {
     static int per_sm[64] = {0};
@@ -1423,8 +1523,11 @@ size_t residual_partials_needed(const OpDesc& op) {
         return std::max(n1, (size_t)box_res_reg_grid(op).x);
     }
     if (op.kind == OP_STENCIL) {
+        // either kernel may run for the 7-point operator (the register-blocked one needs
+        // aligned vectors)
         const dim3 g = stencil_grid(op, KZ_RES);
-        return (size_t)g.x * g.y * g.z;
+        const size_t n1 = (size_t)g.x * g.y * g.z;
+        return star_reg_shape(op) ? std::max(n1, (size_t)star_res_grid(op).x) : n1;
     }
     return (size_t)vec_blocks(op.n);
 }
@@ -1440,6 +1543,12 @@ cudaError_t launch_residual(const OpDesc& op, const double* b, const double* x, 
         const dim3 grid = box_grid(op), block(BX, BY);
         if (op.dim == 3) k_residual_box<3><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode, 1.0);
         else k_residual_box<2><<<grid, block, 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz, partials, ctl, mode, 1.0);
+        return cudaGetLastError();
+    }
+    if (op.kind == OP_STENCIL && star_reg_shape(op) && (uintptr_t)b % 16 == 0 && (uintptr_t)x % 16 == 0 &&
+        (!r || (uintptr_t)r % 16 == 0) && (!r32 || (uintptr_t)r32 % 8 == 0)) {
+        k_residual_star_reg<<<star_res_grid(op), dim3(32, BOXW), 0, st>>>(b, x, r, r32, op.nx, op.ny, op.nz,
+                                                                          2.0 * op.dim, partials, ctl, mode, 1.0);
         return cudaGetLastError();
     }
     if (op.kind == OP_STENCIL) {
