@@ -1208,33 +1208,38 @@ dim3 box_grid(const OpDesc& op) {
 dim3 box_pair_grid(const OpDesc& op) {
     return dim3((op.nx + 2 * BX - 1) / (2 * BX), (op.ny + BY - 1) / BY, op.dim == 3 ? (op.nz + KBP - 1) / KBP : 1);
 }
-// FP64 register-blocked box step: 3D, nx even and 16-byte aligned vectors. The grid is the
-// blocks resident at once (the fewest over the step's instantiations), at most one warp per
-// (warp column, plane) unit.
-template <typename T>
-int box_reg_per_sm() {
-    static int per_sm[64] = {0};
+// The register-blocked persistent kernels (box steps and residual for 3D grids with nx even,
+// 7-point FP64 step and residual): the grid is the blocks of 32 x BOXW threads resident at
+// once for the least of a kernel family's instantiations (cached per device), and at most one
+// warp per (warp column, plane) unit.
+template <typename... K>
+int resident_per_sm(int (&cache)[64], K... kernels) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (!per_sm[dev]) {
-        int m = 1 << 30, b = 0;
-        const int nt = 32 * BOXW;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<T, BOXY, true, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<T, BOXY, false, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<T, BOXY, true, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_box_reg<T, BOXY, false, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        per_sm[dev] = (m >= 1 && m < (1 << 30)) ? m : 1;
+    if (!cache[dev]) {
+        int m = 1 << 30;
+        for (const void* k : {(const void*)kernels...}) {
+            int b = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 32 * BOXW, 0) == cudaSuccess) m = std::min(m, b);
+        }
+        cache[dev] = (m >= 1 && m < (1 << 30)) ? m : 1;
     }
-    return per_sm[dev];
+    return cache[dev];
+}
+dim3 persistent_grid(const OpDesc& op, int rows_per_thread, int per_sm) {
+    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + rows_per_thread - 1) / rows_per_thread) + 31) / 32;
+    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
+    const int64_t cap = (int64_t)per_sm * device_sm_count();
+    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
 }
 template <typename T>
 dim3 box_reg_grid(const OpDesc& op) {
-    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + BOXY - 1) / BOXY) + 31) / 32;
-    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
-    const int64_t cap = (int64_t)box_reg_per_sm<T>() * device_sm_count();
-    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
+    static int cache[64] = {0};
+    return persistent_grid(op, BOXY,
+                           resident_per_sm(cache, k_cheb_box_reg<T, BOXY, true, false>, k_cheb_box_reg<T, BOXY, false, false>,
+                                           k_cheb_box_reg<T, BOXY, true, true>, k_cheb_box_reg<T, BOXY, false, true>));
 }
-// the grids the register-blocked box kernels take: 3D, nx even, a plane within 32-bit offsets
+// the grids the register-blocked kernels take: 3D, nx even, a plane within 32-bit offsets
 bool box_reg_shape(const OpDesc& op) {
     return op.dim == 3 && op.nx % 2 == 0 && (int64_t)op.nx * op.ny < (int64_t)INT32_MAX;
 }
@@ -1243,62 +1248,21 @@ bool box_reg_ok(const OpDesc& op, const T* p, const T* q, const T* out) {
     const size_t al = 2 * sizeof(T);
     return box_reg_shape(op) && ((uintptr_t)p % al == 0) && ((uintptr_t)out % al == 0) && (!q || (uintptr_t)q % al == 0);
 }
-// FP64 register-blocked 7-point step: the shapes of the box kernels, Poisson weights
-int star_reg_per_sm() {
-    static int per_sm[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (!per_sm[dev]) {
-        int m = 1 << 30, b = 0;
-        const int nt = 32 * BOXW;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_star_reg<true, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_star_reg<false, false>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_star_reg<true, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb_star_reg<false, true>, nt, 0) == cudaSuccess) m = std::min(m, b);
-        per_sm[dev] = (m >= 1 && m < (1 << 30)) ? m : 1;
-    }
-    return per_sm[dev];
-}
+// FP64 register-blocked 7-point step and residual: the shapes of the box kernels, Poisson weights
 dim3 star_reg_grid(const OpDesc& op) {
-    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + STARY - 1) / STARY) + 31) / 32;
-    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
-    const int64_t cap = (int64_t)star_reg_per_sm() * device_sm_count();
-    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
+    static int cache[64] = {0};
+    return persistent_grid(op, STARY,
+                           resident_per_sm(cache, k_cheb_star_reg<true, false>, k_cheb_star_reg<false, false>,
+                                           k_cheb_star_reg<true, true>, k_cheb_star_reg<false, true>));
 }
 bool star_reg_shape(const OpDesc& op) { return !op.box && op.wx == nullptr && box_reg_shape(op); }
-
-int star_res_per_sm() {
-    static int per_sm[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (!per_sm[dev]) {
-        int b = 0;
-        per_sm[dev] = (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_residual_star_reg, 32 * BOXW, 0) == cudaSuccess && b >= 1) ? b : 1;
-    }
-    return per_sm[dev];
-}
 dim3 star_res_grid(const OpDesc& op) {
-    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + STARY - 1) / STARY) + 31) / 32;
-    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
-    const int64_t cap = (int64_t)star_res_per_sm() * device_sm_count();
-    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
-}
-
-int box_res_reg_per_sm() {
-    static int per_sm[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (!per_sm[dev]) {
-        int b = 0;
-        per_sm[dev] = (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_residual_box_reg, 32 * BOXW, 0) == cudaSuccess && b >= 1) ? b : 1;
-    }
-    return per_sm[dev];
+    static int cache[64] = {0};
+    return persistent_grid(op, STARY, resident_per_sm(cache, k_residual_star_reg));
 }
 dim3 box_res_reg_grid(const OpDesc& op) {
-    const int64_t nwc = ((int64_t)(op.nx / 2) * ((op.ny + BOXY - 1) / BOXY) + 31) / 32;
-    const int64_t units = nwc * op.nz, want = (units + BOXW - 1) / BOXW;
-    const int64_t cap = (int64_t)box_res_reg_per_sm() * device_sm_count();
-    return dim3((unsigned)std::max<int64_t>(1, std::min(want, cap)));
+    static int cache[64] = {0};
+    return persistent_grid(op, BOXY, resident_per_sm(cache, k_residual_box_reg));
 }
 bool box_res_reg_ok(const OpDesc& op, const double* b, const double* x, const double* r, const float* r32) {
     return box_reg_shape(op) && ((uintptr_t)b % 16 == 0) && ((uintptr_t)x % 16 == 0) &&
