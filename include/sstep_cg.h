@@ -71,6 +71,7 @@ enum { SSTEP_START_R = 0 };
  *    stencil operator with a constant M (the Poisson or box stencil, or precond NONE; otherwise
  *    SSTEP_ERR_UNSUPPORTED) and block_conjugate = 0. */
 enum { SSTEP_GRAM_FORM_DIRECT = 0, SSTEP_GRAM_FORM_MOMENTS = 1, SSTEP_GRAM_FORM_FUSED = 2 };
+enum { SSTEP_STEP_AUTO = 0, SSTEP_STEP_TMA = 1, SSTEP_STEP_PLAIN = 2 };
 
 #define SSTEP_MAX_S 32
 
@@ -110,6 +111,12 @@ typedef struct {
                               device (sstep_cg_history): the relative residual entering it, the
                               Gram solve's inexactness delta_k (Section 7) and the smallest
                               unscaled G_ii; 0 (default): none */
+    int step_kernel;       /* MIXED, 3D Poisson stencil with nx a multiple of 4: how the FP32
+                              Chebyshev step reads its planes. SSTEP_STEP_AUTO (default): through
+                              tensor-map (TMA) tiles when the step's three vectors exceed the L2
+                              cache, else plain loads; SSTEP_STEP_TMA / SSTEP_STEP_PLAIN force one
+                              (TMA falls back to plain loads where the shape does not allow it).
+                              Both give bitwise the same basis. Elsewhere: unused */
 } sstep_cg_opts;
 
 typedef struct {
@@ -128,6 +135,8 @@ typedef struct {
     float prof_ms[4];          /* profile_every > 0: summed device time of the sampled launches of
                                   [0] Chebyshev steps, [1] Gram + FGS, [2] update, [3] residual */
     int prof_launches[4];      /* number of sampled launches behind each prof_ms entry */
+    int step_tma;              /* 1: the FP32 Chebyshev steps read their planes through tensor-map
+                                  (TMA) tiles (opts.step_kernel), 0: plain loads */
 } sstep_cg_info;
 
 /* Fills *opts with the defaults listed above (s = 8, nu = 25, tol = 1e-8, Jacobi, FGS,

@@ -22,6 +22,7 @@ GRAM_SOLVER = {"fgs": 0, "cholesky": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 PRECOND = {"none": 0, "jacobi": 1}
 GRAM_FORM = {"direct": 0, "moments": 1, "fused": 2}
+STEP_KERNEL = {"auto": 0, "tma": 1, "plain": 2}
 
 
 class Opts(C.Structure):
@@ -31,7 +32,7 @@ class Opts(C.Structure):
                 ("refresh_period", C.c_int), ("max_refresh", C.c_int), ("seed", C.c_uint64),
                 ("use_graph", C.c_int), ("check_every", C.c_int), ("profile_every", C.c_int),
                 ("batch_chunk", C.c_int), ("batch_ctas_per_sm", C.c_int), ("block_conjugate", C.c_int),
-                ("history", C.c_int)]
+                ("history", C.c_int), ("step_kernel", C.c_int)]
 
 
 class Info(C.Structure):
@@ -39,7 +40,7 @@ class Info(C.Structure):
                 ("rel_res_recursive", C.c_double), ("rel_res_true", C.c_double),
                 ("lambda_min_used", C.c_double), ("lambda_max_used", C.c_double), ("min_gii", C.c_double),
                 ("delta_last", C.c_double), ("ms", C.c_float), ("kernel_launches", C.c_int),
-                ("prof_ms", C.c_float * 4), ("prof_launches", C.c_int * 4)]
+                ("prof_ms", C.c_float * 4), ("prof_launches", C.c_int * 4), ("step_tma", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -142,6 +143,8 @@ def sstep_cg_default_opts(**overrides) -> Opts:
             v = PRECOND[v]
         elif k == "gram_form" and isinstance(v, str):
             v = GRAM_FORM[v]
+        elif k == "step_kernel" and isinstance(v, str):
+            v = STEP_KERNEL[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)

@@ -29,6 +29,8 @@ struct sstep_cg_s {
     int64_t ld = 0;
     bool mixed = false;         // FP32 basis (form 1)
     float* P32 = nullptr;       // mixed form: FP32 basis, same layout as P
+    bool tma = false;           // mixed form: FP32 steps through tensor-map tiles (step_kernel)
+    std::vector<CUtensorMap> tmaps;   // per FP32 column j: [2j] read as p, [2j + 1] read as q
     float* ops32 = nullptr;     // mixed form: FP32 copies of the operator arrays
     double* rtrue = nullptr;    // true residual b - A x
     double* gram_partials = nullptr;
@@ -129,6 +131,10 @@ sstep_status validate_opts(sstep_cg_t h, const sstep_cg_opts* o) {
     if (o->check_every < 1) { set_err(h, "check_every < 1"); return SSTEP_ERR_INVALID_ARG; }
     if (o->profile_every < 0) { set_err(h, "profile_every < 0"); return SSTEP_ERR_INVALID_ARG; }
     if (o->history < 0 || o->history > (1 << 20)) { set_err(h, "history outside [0, 2^20]"); return SSTEP_ERR_INVALID_ARG; }
+    if (o->step_kernel < SSTEP_STEP_AUTO || o->step_kernel > SSTEP_STEP_PLAIN) {
+        set_err(h, "step_kernel must be SSTEP_STEP_AUTO, _TMA or _PLAIN");
+        return SSTEP_ERR_INVALID_ARG;
+    }
     return SSTEP_OK;
 }
 
@@ -415,6 +421,21 @@ sstep_status finish_create(sstep_cg_t h) {
     if (h->mixed) {
         CK(cudaMalloc(&h->P32, sizeof(float) * h->ld * (h->opts.s + 1)));
         if ((st = make_f32_operator(h)) != SSTEP_OK) return st;
+        // FP32 steps through TMA tiles: forced, or (AUTO) when the step's three FP32 vectors
+        // exceed L2 (below that the plain-load kernel is faster); plain loads when the shape
+        // or the driver does not allow it
+        int l2 = 0;
+        CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device));
+        const bool want = h->opts.step_kernel == SSTEP_STEP_TMA ||
+                          (h->opts.step_kernel == SSTEP_STEP_AUTO && 3.0 * sizeof(float) * (double)n > (double)l2);
+        if (want && step_tma_shape(h->op)) {
+            h->tmaps.resize(2 * (size_t)(h->opts.s + 1));
+            bool ok = true;
+            for (int j = 0; j <= h->opts.s && ok; ++j)
+                ok = step_tma_maps(h->op, h->P32 + (int64_t)j * h->ld, &h->tmaps[2 * j], &h->tmaps[2 * j + 1]) == cudaSuccess;
+            h->tma = ok;
+            if (!ok) h->tmaps.clear();
+        }
     }
     CK(cudaMalloc(&h->rtrue, sizeof(double) * n));
     if (h->opts.history > 0) {
@@ -429,7 +450,7 @@ sstep_status finish_create(sstep_cg_t h) {
                        "box stencil, or precond NONE)");
             return SSTEP_ERR_UNSUPPORTED;
         }
-        h->mom_nblk = cheb_step_blocks(h->op, h->mixed);
+        h->mom_nblk = cheb_step_blocks(h->op, h->mixed, h->tma);
         CK(cudaMalloc(&h->mom_part, (size_t)16 * h->mom_nblk * h->opts.s));
         CK(cudaMalloc(&h->mom_part2, sizeof(double) * MAX_FIN_BLOCKS * 2 * h->opts.s));
     }
@@ -507,7 +528,11 @@ sstep_status launch_outer(sstep_cg_t h, const double* b, double* x, int* launche
             const float* p = h->P32 + (int64_t)j * h->ld;
             const float* q = j > 0 ? h->P32 + (int64_t)(j - 1) * h->ld : nullptr;
             float* o = h->P32 + (int64_t)(j + 1) * h->ld;
-            CK(launch_cheb_step<float>(h->op, p, q, o, h->theta, h->sigma, j == 0, h->jacobi, h->ctl, h->stream, mom));
+            if (h->tma)
+                CK(launch_cheb_step_tma(h->op, h->tmaps[2 * j], h->tmaps[j > 0 ? 2 * j - 1 : 2 * j], o, h->theta,
+                                        h->sigma, j == 0, h->jacobi, h->ctl, h->stream, mom));
+            else
+                CK(launch_cheb_step<float>(h->op, p, q, o, h->theta, h->sigma, j == 0, h->jacobi, h->ctl, h->stream, mom));
         } else {
             const double* p = h->P + (int64_t)j * h->ld;
             const double* q = j > 0 ? h->P + (int64_t)(j - 1) * h->ld : nullptr;
@@ -743,6 +768,7 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
             continue;
         }
         if (done == NUMERICAL) status = SSTEP_ERR_NUMERICAL;
+        else if (done == TIMED_OUT) status = SSTEP_ERR_TIMEOUT;
         else if (done == MAX_OUTER || !true_ok) status = SSTEP_ERR_NO_CONVERGENCE;
         break;
     }
@@ -763,6 +789,7 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
     inf.delta_last = c.delta;
     inf.ms = ms;
     inf.kernel_launches = launches;
+    inf.step_tma = h->tma ? 1 : 0;
     if (info) *info = inf;
     if (status != SSTEP_OK)
         set_err(h, "solve ended with %s after %d outer iterations (true rel. residual %.3e)",
@@ -802,6 +829,8 @@ void sstep_cg_default_opts(sstep_cg_opts* o) {
     o->batch_chunk = 0;
     o->batch_ctas_per_sm = 0;
     o->block_conjugate = 0;
+    o->history = 0;
+    o->step_kernel = SSTEP_STEP_AUTO;
 }
 
 sstep_status sstep_cg_create_csr(sstep_cg_t* out, int64_t n, const int32_t* rowptr_d, const int32_t* colind_d,

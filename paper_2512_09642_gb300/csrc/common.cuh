@@ -12,8 +12,9 @@ namespace sstep {
 constexpr int MAXS = SSTEP_MAX_S;
 constexpr int MAXC = MAXS + 1;            // basis columns p_0 .. p_s
 
-// Termination states written by the Gram kernel's last block into Ctl::done.
-enum Done : int { RUNNING = 0, CONVERGED = 1, MAX_OUTER = 2, NUMERICAL = 3 };
+// Termination states written by the Gram kernel's last block into Ctl::done (TIMED_OUT: a
+// bounded device-side wait of a step kernel expired).
+enum Done : int { RUNNING = 0, CONVERGED = 1, MAX_OUTER = 2, NUMERICAL = 3, TIMED_OUT = 4 };
 
 // Device-resident control block of one handle. Kernels of an outer iteration communicate
 // through it (the Gram solve writes alpha/beta, the update reads them), and every kernel

@@ -272,6 +272,146 @@ __global__ void __launch_bounds__(BX* BY) k_cheb_poisson_pair(const T* __restric
     if (GRAM) mom_block_store(acc, mom, nblk);
 }
 
+// FP32 7-point step through tensor-map tiles (3D, nx a multiple of 4). The mixed form's FP32
+// step is memory-bound and its loads wait on HBM: with the loads in registers the pair kernel
+// runs at 0.78 of the measured HBM rate at 256^3. Here each block's 64 x 8 tile of a 32-plane
+// slab arrives by TMA into a ring of STMA shared-memory stages tracked by mbarriers: plane k
+// of p as a 72 x 10 box (x from i0 - 4, so the x coordinate stays on a 16-byte boundary, and
+// y from j0 - 1; the hardware fills what lies outside the grid with zeros, the Dirichlet
+// values) together with the tile of q. One thread issues the copies; every thread reads its
+// pair, its x and y neighbours and the next plane's pair from shared memory. The sums and
+// their order are those of k_cheb_poisson_pair (bitwise equal outputs). Every wait is bounded:
+// one that expires sets ctl->done = TIMED_OUT, the block leaves the plane loop with all its
+// threads, waits (bounded) for its copies in flight and returns. Measured at 256^3: 0.0382 ->
+// 0.0349 ms per step, 0.0401 -> 0.0362 with the fused moments (0.86 and 0.83 of HBM); at
+// 192^3, where a step's three vectors fit in L2, the pair kernel is faster (0.0144 against
+// 0.0176 ms), so the host picks this kernel only when they do not.
+constexpr int TMX = 64, TMY = 8, TMKZ = 32, STMA = 6;
+constexpr int TPX = TMX + 8, TPY = TMY + 2;   // the p box: x from i0 - 4, y from j0 - 1
+constexpr uint32_t TP_BYTES = TPX * TPY * 4, TQ_BYTES = TMX * TMY * 4;
+constexpr int TP_STRIDE = (TP_BYTES + 127) / 128 * 128, TQ_STRIDE = (TQ_BYTES + 127) / 128 * 128;
+constexpr int TSTAGE = TP_STRIDE + TQ_STRIDE;
+constexpr long long TMA_WAIT_LIMIT = 1ll << 22;   // polls of one wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders this thread's earlier generic accesses of shared memory before later TMA writes
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// false when the phase of the given parity has not completed after TMA_WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity) {
+    for (long long it = 0; it < TMA_WAIT_LIMIT; ++it)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <bool FIRST, bool GRAM>
+__global__ void __launch_bounds__(32 * TMY, 6) k_cheb_poisson_tma(const __grid_constant__ CUtensorMap tp,
+                                                                  const __grid_constant__ CUtensorMap tq,
+                                                                  float* __restrict__ out, int nx, int ny, int nz,
+                                                                  float c1, float c2, Ctl* __restrict__ ctl, float one,
+                                                                  void* mom, int nblk) {
+    if (ctl->done) return;
+    __shared__ alignas(128) unsigned char sbuf[STMA * TSTAGE];
+    __shared__ alignas(8) unsigned long long bar[STMA];
+    __shared__ int aborted;
+    const int lane = threadIdx.x, w = threadIdx.y, tid = lane + 32 * w;
+    const int i0 = blockIdx.x * TMX, j0 = blockIdx.y * TMY;
+    const int k0 = blockIdx.z * TMKZ, k1 = min(nz, k0 + TMKZ);
+    const int npl = k1 - k0 + 2;   // planes k0 - 1 .. k1, plane t = k0 - 1 + t in stage t % STMA
+    auto sp = [&](int t) { return reinterpret_cast<const float*>(sbuf + (t % STMA) * TSTAGE); };
+    auto sq = [&](int t) { return reinterpret_cast<const float*>(sbuf + (t % STMA) * TSTAGE + TP_STRIDE); };
+    auto issue = [&](int t) {
+        const int s = t % STMA, kk = k0 - 1 + t;
+        const bool wq = !FIRST && kk >= k0 && kk < k1;
+        mbar_expect_tx(&bar[s], TP_BYTES + (wq ? TQ_BYTES : 0u));
+        tma_load_3d(sbuf + s * TSTAGE, &tp, i0 - 4, j0 - 1, kk, &bar[s]);
+        if (wq) tma_load_3d(sbuf + s * TSTAGE + TP_STRIDE, &tq, i0, j0, kk, &bar[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < STMA; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+        aborted = 0;
+    }
+    __syncthreads();
+    int issued = 0;   // thread 0's count of planes issued
+    if (tid == 0) {
+        issued = STMA < npl ? STMA : npl;
+        for (int t = 0; t < issued; ++t) issue(t);
+    }
+    auto wait_plane = [&](int t) {
+        if (!mbar_wait(&bar[t % STMA], (uint32_t)((t / STMA) & 1))) {
+            aborted = 1;
+            atomicExch(&ctl->done, (int)TIMED_OUT);
+        }
+    };
+    const int i = i0 + 2 * lane, j = j0 + w;
+    const bool in = i < nx && j < ny;   // nx even: i + 1 < nx as well
+    const int cx = 4 + 2 * lane;        // the pair's column in the p box
+    MomAcc<float> acc;
+    wait_plane(0);
+    float2 pdn = *reinterpret_cast<const float2*>(sp(0) + (w + 1) * TPX + cx);
+    wait_plane(1);
+    for (int k = k0; k < k1; ++k) {
+        const int t = k - k0 + 1;
+        wait_plane(t + 1);
+        const float* P = sp(t);
+        const float2 pc = *reinterpret_cast<const float2*>(P + (w + 1) * TPX + cx);
+        const float xl = P[(w + 1) * TPX + cx - 1], xr = P[(w + 1) * TPX + cx + 2];
+        const float2 ym = *reinterpret_cast<const float2*>(P + w * TPX + cx);
+        const float2 yp = *reinterpret_cast<const float2*>(P + (w + 2) * TPX + cx);
+        const float2 pup = *reinterpret_cast<const float2*>(sp(t + 1) + (w + 1) * TPX + cx);
+        const float2 qv = FIRST ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(sq(t) + w * TMX + 2 * lane);
+        if (in) {
+            float s0 = add1(add1(xl, pc.y, one), add1(ym.x, yp.x, one), one);
+            float s1 = add1(add1(pc.x, xr, one), add1(ym.y, yp.y, one), one);
+            s0 = add1(s0, add1(pdn.x, pup.x, one), one);
+            s1 = add1(s1, add1(pdn.y, pup.y, one), one);
+            float2 o;
+            o.x = FIRST ? fma(c2, s0, c1 * pc.x) : fma(c2, s0, fma(c1, pc.x, -qv.x));
+            o.y = FIRST ? fma(c2, s1, c1 * pc.y) : fma(c2, s1, fma(c1, pc.y, -qv.y));
+            *reinterpret_cast<float2*>(out + i + (int64_t)nx * j + (int64_t)nx * ny * k) = o;
+            if (GRAM) {
+                acc.add(pc.x, o.x);
+                acc.add(pc.y, o.y);
+            }
+        }
+        pdn = pc;
+        __syncthreads();   // every thread is done with plane t: its stage takes plane t + STMA
+        if (aborted) break;
+        if (tid == 0 && issued < npl) {
+            fence_proxy_async();
+            issue(issued);
+            ++issued;
+        }
+    }
+    if (aborted && tid == 0)   // the copies in flight land before the block's shared memory goes
+        for (int t = 0; t < issued; ++t) mbar_wait(&bar[t % STMA], (uint32_t)((t / STMA) & 1));
+    if (GRAM) mom_block_store<32 * TMY>(acc, mom, nblk);
+}
+
 // CSR Chebyshev step, one thread per row: y = A p, out = cdv (y) - c sigma p - q. A warp's
 // loads of vals / colind are strided by the row length, but the warp's rows share their
 // cache lines, which L1 keeps between the row's iterations: measured at 0.95 (FP64) and 0.93
@@ -1383,8 +1523,75 @@ void cheb_stencil_dispatch(const OpDesc& op, const T* p, const T* q, T* out, dou
 
 }  // namespace
 
-int cheb_step_blocks(const OpDesc& op, bool fp32) {
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// the driver's tensor-map encoder, resolved once (null when the driver has none)
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+// an nx x ny x nz FP32 array read in bx x by x 1 boxes, zeros outside
+bool encode_box_map(float* base, const OpDesc& op, int bx, int by, CUtensorMap* m) {
+    const cuuint64_t gdim[3] = {(cuuint64_t)op.nx, (cuuint64_t)op.ny, (cuuint64_t)op.nz};
+    const cuuint64_t gstride[2] = {(cuuint64_t)op.nx * 4, (cuuint64_t)op.nx * op.ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    return encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, gdim, gstride, box, estride,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+dim3 step_tma_grid(const OpDesc& op) {
+    return dim3((op.nx + TMX - 1) / TMX, (op.ny + TMY - 1) / TMY, (op.nz + TMKZ - 1) / TMKZ);
+}
+}  // namespace
+
+bool step_tma_shape(const OpDesc& op) {
+    return op.kind == OP_STENCIL && !op.box && op.wx == nullptr && op.dim == 3 && op.nx % 4 == 0 && op.nx >= 4 &&
+           op.ny >= 1 && op.nz >= 1;
+}
+
+cudaError_t step_tma_maps(const OpDesc& op, float* column, CUtensorMap* mp, CUtensorMap* mq) {
+    if (!step_tma_shape(op) || (uintptr_t)column % 16 != 0 || !encode_tiled()) return cudaErrorNotSupported;
+    if (!encode_box_map(column, op, TPX, TPY, mp) || !encode_box_map(column, op, TMX, TMY, mq))
+        return cudaErrorNotSupported;
+    return cudaSuccess;
+}
+
+cudaError_t launch_cheb_step_tma(const OpDesc& op, const CUtensorMap& mp, const CUtensorMap& mq, float* out,
+                                 double theta, double sigma, bool first, bool jacobi, Ctl* ctl, cudaStream_t st,
+                                 void* mom) {
+    if (!step_tma_shape(op)) return cudaErrorInvalidValue;
+    // the constants of cheb_stencil_dispatch's Poisson branch
+    const double c = first ? theta : 2.0 * theta, d2 = 2.0 * op.dim;
+    const float c1 = (float)(jacobi ? c * (1.0 - sigma) : c * (d2 - sigma));
+    const float c2 = (float)(jacobi ? -c / d2 : -c);
+    const dim3 g = step_tma_grid(op), block(32, TMY);
+    const int nb = (int)(g.x * g.y * g.z);
+    if (first) {
+        if (mom) k_cheb_poisson_tma<true, true><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, mom, nb);
+        else k_cheb_poisson_tma<true, false><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, nullptr, nb);
+    } else {
+        if (mom) k_cheb_poisson_tma<false, true><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, mom, nb);
+        else k_cheb_poisson_tma<false, false><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, nullptr, nb);
+    }
+    return cudaGetLastError();
+}
+
+int cheb_step_blocks(const OpDesc& op, bool fp32, bool tma) {
     if (op.kind != OP_STENCIL) return 0;
+    if (tma && fp32 && step_tma_shape(op)) {
+        const dim3 g = step_tma_grid(op);
+        return (int)(g.x * g.y * g.z);
+    }
     const int kz = fp32 ? kz_step<float>() : kz_step<double>();
     dim3 g;
     if (op.box) {

@@ -1,6 +1,8 @@
 // Host-side launchers of the library's kernels (internal; not part of the C ABI).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap
+
 #include "common.cuh"
 
 namespace sstep {
@@ -42,8 +44,21 @@ template <typename T>
 cudaError_t launch_cheb_step(const OpDesc& op, const T* p, const T* q, T* out, double theta,
                              double sigma, bool first, bool jacobi, const Ctl* ctl, cudaStream_t st,
                              void* mom = nullptr);
-// Blocks of the stencil step kernel launch_cheb_step uses for op in FP32 or FP64 (0 for CSR).
-int cheb_step_blocks(const OpDesc& op, bool fp32);
+// Blocks of the stencil step kernel launch_cheb_step uses for op in FP32 or FP64 (0 for CSR),
+// or, with tma, those of launch_cheb_step_tma.
+int cheb_step_blocks(const OpDesc& op, bool fp32, bool tma = false);
+
+// FP32 7-point Poisson step through tensor-map (TMA) tiles: 3D, nx a multiple of 4. Each
+// basis column needs two maps, made once: `mp` (the column read as p, tiles with a halo) and
+// `mq` (read as q). step_tma_maps returns cudaErrorNotSupported when the shape does not allow
+// it or the driver has no tensor-map encoder. launch_cheb_step_tma computes the same step as
+// launch_cheb_step<float> (bitwise) from the maps of p and q (mq unused when first); a
+// bounded wait that expires sets ctl->done = TIMED_OUT.
+bool step_tma_shape(const OpDesc& op);
+cudaError_t step_tma_maps(const OpDesc& op, float* column, CUtensorMap* mp, CUtensorMap* mq);
+cudaError_t launch_cheb_step_tma(const OpDesc& op, const CUtensorMap& mp, const CUtensorMap& mq, float* out,
+                                 double theta, double sigma, bool first, bool jacobi, Ctl* ctl, cudaStream_t st,
+                                 void* mom = nullptr);
 
 // r = b - A x in FP64; writes r (double, if non-null) and, if r32 != null, the FP32 copy
 // scaled by ctl->scale_next (mode 2); reduces ||r||^2 through `partials` (one double per

@@ -70,6 +70,7 @@ def test_default_options(abi):
     assert (o.s, o.nu, o.tol, o.max_outer) == (8, 25, 1e-8, 100000)
     assert o.bounds_mode == abi.BOUNDS["gersh_lanczos10"] and o.precond == abi.PRECOND["jacobi"]
     assert o.gram_solver == abi.GRAM_SOLVER["fgs"] and o.precision == abi.PRECISION["fp64"]
+    assert o.step_kernel == abi.STEP_KERNEL["auto"] and o.history == 0
 
 
 @pytest.mark.parametrize("bad", [dict(s=0), dict(s=33), dict(nu=0), dict(tol=0.0), dict(tol=-1.0),
@@ -125,11 +126,12 @@ def test_status_strings(abi):
         assert abi.sstep_cg_status_string(code) == name
 
 
-@pytest.mark.parametrize("bad", [dict(gram_form=3), dict(gram_form=2, block_conjugate=1), dict(refresh_period=0)])
+@pytest.mark.parametrize("bad", [dict(gram_form=3), dict(gram_form=2, block_conjugate=1), dict(refresh_period=0),
+                                 dict(step_kernel=3), dict(step_kernel=-1)])
 def test_gram_form_and_refresh_options_checked_on_host(abi, bad):
     """FUSED (the moments reduced by the step kernels) does not combine with the block
-    conjugation (SSTEP_ERR_UNSUPPORTED); an unknown form or a refresh period below 1 is an
-    invalid argument. All rejected before any CUDA call."""
+    conjugation (SSTEP_ERR_UNSUPPORTED); an unknown form, a refresh period below 1 or an unknown
+    step_kernel is an invalid argument. All rejected before any CUDA call."""
     with pytest.raises(abi.SStepError) as ei:
         abi.sstep_cg_create_stencil(3, 8, 8, 8, None, abi.sstep_cg_default_opts(**bad), stream=0)
     assert ei.value.status == (7 if bad.get("block_conjugate") else 1)

@@ -172,3 +172,68 @@ def test_mixed_fused_first_iterate_at_fp32_level():
         x, info = sv.solve(_dev(p.b))
         assert info["outer_iters"] == k
         assert _rel(x.cpu().numpy(), ref.history[k - 1].x) <= 1e-5, k
+
+
+# The FP32 Chebyshev step through tensor-map (TMA) tiles (3D Poisson, nx a multiple of 4) against
+# the same step with plain loads: the same sums in the same order, so with the separate Gram pass
+# (moments form) the solves agree bit for bit. With the fused moments the per-block partial sums
+# follow each kernel's blocks (32-plane slabs against 16), so there the iterates agree to FP32
+# rounding. Grids: 64 x 13 x 11 (one x tile, ragged y and z tiles against 64 x 8 x 32), 4 x 3 x 70
+# (a 4-point-wide grid inside one 64-wide tile, three 32-plane slabs), 132 x 37 x 35 (a 4-point x
+# tile at the end, both x faces inside boxes that start 4 points before the tile).
+TMA_GRIDS = [((64, 13, 11), 41), ((4, 3, 70), 42), ((132, 37, 35), 43)]
+
+
+@pytest.mark.parametrize("dims,cfg", TMA_GRIDS, ids=["x".join(map(str, d)) for d, _ in TMA_GRIDS])
+@pytest.mark.parametrize("form,period", [("moments", 1), ("moments", 3), ("fused", 1), ("fused", 4)])
+def test_fp32_step_through_tma_tiles_equals_plain_loads(dims, cfg, form, period):
+    p = W.make("p3t", dims, config=cfg)
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "lanczos10", W.lanczos_start(p.n))
+    b = _dev(p.b)
+    for k, tol in ((1, 1e-30), (3, 1e-30), (100000, 1e-8)):
+        out = {}
+        for path in ("tma", "plain"):
+            sv = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=tol, max_outer=k, check_every=1,
+                         precision="mixed", gram_form=form, refresh_period=period, step_kernel=path)
+            x, info = sv.solve(b)
+            out[path] = (x.cpu().numpy(), info)
+            sv.close()
+        (xt, it), (xp, ip) = out["tma"], out["plain"]
+        assert it["step_tma"] == 1 and ip["step_tma"] == 0
+        if form == "moments":
+            assert it["outer_iters"] == ip["outer_iters"], (k, it["outer_iters"], ip["outer_iters"])
+            assert np.array_equal(xt, xp), (k, _rel(xt, xp))
+        elif tol < 1e-20:
+            assert _rel(xt, xp) <= 1e-5, (k, _rel(xt, xp))
+        if tol == 1e-8:
+            assert it["status"] == "SSTEP_OK" and it["rel_res_true"] <= 1e-8
+
+
+def test_fp32_step_tma_falls_back_where_the_shape_does_not_allow_it():
+    """nx not a multiple of 4 (a TMA row stride must be a multiple of 16 bytes), and 2D: plain
+    loads, the same solve."""
+    for dims, cfg in (((70, 13, 11), 44), ((64, 45), 45)):
+        p = W.make("p3t", dims, config=cfg)
+        op = O.Operator(*p.csr())
+        lam = OS.bounds(op, "lanczos10", W.lanczos_start(p.n))
+        xs = {}
+        for path in ("tma", "plain"):
+            sv = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-8, precision="mixed", gram_form="moments",
+                         step_kernel=path)
+            x, info = sv.solve(_dev(p.b))
+            assert info["step_tma"] == 0 and info["status"] == "SSTEP_OK"
+            xs[path] = x.cpu().numpy()
+            sv.close()
+        assert np.array_equal(xs["tma"], xs["plain"])
+
+
+def test_fp32_step_auto_uses_tma_only_when_the_step_exceeds_l2():
+    """AUTO: plain loads at 64^3 (3 x 1 MB of FP32 vectors), TMA tiles at 256^3 (3 x 67 MB > L2)."""
+    for side, want in ((64, 0), (256, 1)):
+        p = W.poisson3d(side)
+        sv = _solver(p, "stencil", bounds=(0.003, 2.0), s=8, nu=25, tol=1e-30, max_outer=1, precision="mixed",
+                     gram_form="fused")
+        _, info = sv.solve(_dev(p.b))
+        assert info["step_tma"] == want, side
+        sv.close()
