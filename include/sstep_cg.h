@@ -345,6 +345,16 @@ SSTEP_API sstep_status sstep_gram_fgs_noalloc(int64_t n, int s, int nu, int gram
                                               int64_t ldp, const double* mdiag_d, double mconst,
                                               double lambda_min, double lambda_max, double* out_d, void* stream);
 
+/* Self-test of the bounded device-side waits of the mixed form's TMA step (the path
+ * opts.step_kernel selects): runs that kernel once on a 64 x 8 x 4 grid of its own whose
+ * shared-memory stages expect 16 bytes more than their tensor-map copies deliver, so that no
+ * wait completes, with a limit of 4096 polls per wait. *done_state (host) receives the
+ * control block's termination state afterwards: 4 (timed out) is the designed outcome, and
+ * the CUDA context stays usable. Returns SSTEP_ERR_UNSUPPORTED when the driver has no
+ * tensor-map encoder, SSTEP_ERR_CUDA when a CUDA call failed, SSTEP_ERR_INVALID_ARG for a
+ * null pointer. Allocates and frees its own 64 KB on the current device (synchronous). */
+SSTEP_API sstep_status sstep_selftest_tma_timeout(int* done_state);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,7 @@ _SIGS = {
     "sstep_coarse_fgs": (_I, [_VP, _I, _I, _I, _VP, _VP, _I, _I]),
     "sstep_gram_fgs_noalloc": (_I, [_I64, _I, _I, _I, _VP, _I64, _VP, _D, _D, _D, _VP, _VP]),
     "sstep_cg_history": (_I, [_VP, C.POINTER(C.c_double), _I, C.POINTER(C.c_int)]),
+    "sstep_selftest_tma_timeout": (_I, [C.POINTER(C.c_int)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -332,3 +333,11 @@ def sstep_cg_history(h, capacity: int):
 
 def exported_names():
     return sorted(_SIGS)
+
+
+def sstep_selftest_tma_timeout() -> int:
+    """Runs the TMA step's bounded-wait self-test; returns the control block's state after it
+    (4 = timed out, the designed outcome)."""
+    st = C.c_int(-1)
+    _check(lib.sstep_selftest_tma_timeout(C.byref(st)), None)
+    return st.value

@@ -1192,4 +1192,18 @@ sstep_status sstep_cg_lanczos(sstep_cg_t h, int k, uint64_t seed, double* alpha_
     return SSTEP_OK;
 }
 
+sstep_status sstep_selftest_tma_timeout(int* done_state) {
+    if (!done_state) return SSTEP_ERR_INVALID_ARG;
+    const cudaError_t e = tma_wait_selftest(done_state);
+    if (e == cudaErrorNotSupported) {
+        sstep::set_global_error("no tensor-map encoder in this driver");
+        return SSTEP_ERR_UNSUPPORTED;
+    }
+    if (e != cudaSuccess) {
+        sstep::set_global_error(cudaGetErrorString(e));
+        return SSTEP_ERR_CUDA;
+    }
+    return SSTEP_OK;
+}
+
 }  // extern "C"

@@ -312,9 +312,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t pa
         : "memory");
     return ok != 0;
 }
-// false when the phase of the given parity has not completed after TMA_WAIT_LIMIT polls
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity) {
-    for (long long it = 0; it < TMA_WAIT_LIMIT; ++it)
+// false when the phase of the given parity has not completed after `limit` polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try_wait(b, parity)) return true;
     return false;
 }
@@ -332,7 +332,10 @@ __global__ void __launch_bounds__(32 * TMY, 6) k_cheb_poisson_tma(const __grid_c
                                                                   const __grid_constant__ CUtensorMap tq,
                                                                   float* __restrict__ out, int nx, int ny, int nz,
                                                                   float c1, float c2, Ctl* __restrict__ ctl, float one,
-                                                                  void* mom, int nblk) {
+                                                                  void* mom, int nblk, uint32_t extra_tx,
+                                                                  long long wait_limit) {
+    // extra_tx > 0 (the self-test of the bounded waits only): every stage expects that many
+    // bytes more than its copies deliver, so no wait completes
     if (ctl->done) return;
     __shared__ alignas(128) unsigned char sbuf[STMA * TSTAGE];
     __shared__ alignas(8) unsigned long long bar[STMA];
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(32 * TMY, 6) k_cheb_poisson_tma(const __grid_c
     auto issue = [&](int t) {
         const int s = t % STMA, kk = k0 - 1 + t;
         const bool wq = !FIRST && kk >= k0 && kk < k1;
-        mbar_expect_tx(&bar[s], TP_BYTES + (wq ? TQ_BYTES : 0u));
+        mbar_expect_tx(&bar[s], TP_BYTES + (wq ? TQ_BYTES : 0u) + extra_tx);
         tma_load_3d(sbuf + s * TSTAGE, &tp, i0 - 4, j0 - 1, kk, &bar[s]);
         if (wq) tma_load_3d(sbuf + s * TSTAGE + TP_STRIDE, &tq, i0, j0, kk, &bar[s]);
     };
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(32 * TMY, 6) k_cheb_poisson_tma(const __grid_c
         for (int t = 0; t < issued; ++t) issue(t);
     }
     auto wait_plane = [&](int t) {
-        if (!mbar_wait(&bar[t % STMA], (uint32_t)((t / STMA) & 1))) {
+        if (!mbar_wait(&bar[t % STMA], (uint32_t)((t / STMA) & 1), wait_limit)) {
             aborted = 1;
             atomicExch(&ctl->done, (int)TIMED_OUT);
         }
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(32 * TMY, 6) k_cheb_poisson_tma(const __grid_c
         }
     }
     if (aborted && tid == 0)   // the copies in flight land before the block's shared memory goes
-        for (int t = 0; t < issued; ++t) mbar_wait(&bar[t % STMA], (uint32_t)((t / STMA) & 1));
+        for (int t = 0; t < issued; ++t) mbar_wait(&bar[t % STMA], (uint32_t)((t / STMA) & 1), wait_limit);
     if (GRAM) mom_block_store<32 * TMY>(acc, mom, nblk);
 }
 
@@ -1577,13 +1580,46 @@ cudaError_t launch_cheb_step_tma(const OpDesc& op, const CUtensorMap& mp, const 
     const dim3 g = step_tma_grid(op), block(32, TMY);
     const int nb = (int)(g.x * g.y * g.z);
     if (first) {
-        if (mom) k_cheb_poisson_tma<true, true><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, mom, nb);
-        else k_cheb_poisson_tma<true, false><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, nullptr, nb);
+        if (mom) k_cheb_poisson_tma<true, true><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, mom, nb, 0u, TMA_WAIT_LIMIT);
+        else k_cheb_poisson_tma<true, false><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, nullptr, nb, 0u, TMA_WAIT_LIMIT);
     } else {
-        if (mom) k_cheb_poisson_tma<false, true><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, mom, nb);
-        else k_cheb_poisson_tma<false, false><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, nullptr, nb);
+        if (mom) k_cheb_poisson_tma<false, true><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, mom, nb, 0u, TMA_WAIT_LIMIT);
+        else k_cheb_poisson_tma<false, false><<<g, block, 0, st>>>(mp, mq, out, op.nx, op.ny, op.nz, c1, c2, ctl, 1.f, nullptr, nb, 0u, TMA_WAIT_LIMIT);
     }
     return cudaGetLastError();
+}
+
+cudaError_t tma_wait_selftest(int* done_state) {
+    *done_state = -1;
+    OpDesc op{};
+    op.kind = OP_STENCIL;
+    op.dim = 3;
+    op.nx = 64;
+    op.ny = 8;
+    op.nz = 4;
+    op.n = (int64_t)op.nx * op.ny * op.nz;
+    float* v = nullptr;
+    Ctl* ctl = nullptr;
+    cudaError_t e = cudaMalloc(&v, sizeof(float) * 2 * op.n);
+    if (e == cudaSuccess) e = cudaMalloc(&ctl, sizeof(Ctl));
+    CUtensorMap mp, mq;
+    if (e == cudaSuccess) e = cudaMemset(v, 0, sizeof(float) * 2 * op.n);
+    if (e == cudaSuccess) e = cudaMemset(ctl, 0, sizeof(Ctl));
+    if (e == cudaSuccess) e = step_tma_maps(op, v, &mp, &mq);
+    if (e == cudaSuccess) {
+        // one block; its copies deliver 16 bytes less than each stage expects, and each wait
+        // gives up after 4096 polls
+        k_cheb_poisson_tma<false, false><<<step_tma_grid(op), dim3(32, TMY)>>>(mp, mq, v + op.n, op.nx, op.ny, op.nz,
+                                                                              1.f, -1.f, ctl, 1.f, nullptr, 1, 16u, 4096);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    Ctl h{};
+    if (e == cudaSuccess) e = cudaMemcpy(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) *done_state = h.done;
+    cudaFree(v);
+    cudaFree(ctl);
+    return e;
 }
 
 int cheb_step_blocks(const OpDesc& op, bool fp32, bool tma) {

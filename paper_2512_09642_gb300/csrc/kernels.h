@@ -59,6 +59,10 @@ cudaError_t step_tma_maps(const OpDesc& op, float* column, CUtensorMap* mp, CUte
 cudaError_t launch_cheb_step_tma(const OpDesc& op, const CUtensorMap& mp, const CUtensorMap& mq, float* out,
                                  double theta, double sigma, bool first, bool jacobi, Ctl* ctl, cudaStream_t st,
                                  void* mom = nullptr);
+// Self-test of the TMA step's bounded waits: one launch on a 64 x 8 x 4 grid whose stages
+// expect more bytes than their copies deliver, with a short wait limit; done_state receives
+// the control block's state afterwards (TIMED_OUT when the waits gave up as designed).
+cudaError_t tma_wait_selftest(int* done_state);
 
 // r = b - A x in FP64; writes r (double, if non-null) and, if r32 != null, the FP32 copy
 // scaled by ctl->scale_next (mode 2); reduces ||r||^2 through `partials` (one double per

@@ -9,6 +9,9 @@ the documented status code.
   * a recursive residual that converges while the true residual b - A x does not, with no
     restart allowed (max_refresh = 0) -> SSTEP_ERR_NO_CONVERGENCE; with restarts allowed the
     same solve replaces the residual and reaches the tolerance.
+  * a bounded device-side wait that runs out (the TMA step's self-test: its stages expect more
+    bytes than their copies deliver, so no wait completes) -> the TIMED_OUT state (4) instead
+    of a hang, with the context usable afterwards.
 """
 import numpy as np
 import pytest
@@ -103,3 +106,14 @@ def test_max_outer_gives_no_convergence_with_last_iterate():
     x, info = sv.solve(_dev(p.b))
     assert info["status"] == "SSTEP_ERR_NO_CONVERGENCE" and info["outer_iters"] == 3
     assert 1e-8 < info["rel_res_true"] < 1.0
+
+
+def test_tma_step_bounded_waits_time_out_and_leave_the_context_usable():
+    from paper_2512_09642_gb300 import abi
+    assert abi.sstep_selftest_tma_timeout() == 4
+    assert torch.cuda.synchronize() is None   # no sticky error
+    p = W.make("p3t", (64, 13, 11), config=41)
+    sv = _solver(p, "stencil", s=8, nu=25, tol=1e-8, precision="mixed", gram_form="fused", step_kernel="tma")
+    _, info = sv.solve(_dev(p.b))
+    assert info["status"] == "SSTEP_OK" and info["step_tma"] == 1 and info["rel_res_true"] <= 1e-8
+    sv.close()
