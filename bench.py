@@ -998,7 +998,7 @@ def run_spread(args):
 
 
 def run_adjoint(args):
-    """Differentiable solve (the benchmark spec's form 3): 2D diffusion 1024^2, kappa =
+    """Differentiable solve (the adjoint form): 2D diffusion 1024^2, kappa =
     exp(N(0, 0.5^2)), L = ||x - x_target||^2; forward s-step CG (s = 8, nu = 25) to 1e-10, the
     backward adjoint solve (A lambda = 2 (x - x_target), to 1e-9: the attainable accuracy of
     this white-noise right-hand side is about 5e-10) and the dL/dkappa assembly. One step =
