@@ -74,8 +74,10 @@ cudaError_t launch_gram(const GramArgs& g, double* partials, Ctl* ctl, int nbloc
     }
 }
 
+// one finish block per 128 step blocks: its warps' loads of the partials form short chains
+// (measured with 1024 step blocks: 4 finish blocks 30.7 us, 8 blocks 28.7 us, 2 blocks 34.8 us)
 int moments_finish_blocks(int nblk) {
-    const int r = (nblk + 255) / 256;
+    const int r = (nblk + 127) / 128;
     return r < 1 ? 1 : (r > MAX_FIN_BLOCKS ? MAX_FIN_BLOCKS : r);
 }
 
