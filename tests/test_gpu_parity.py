@@ -386,3 +386,46 @@ def test_per_outer_history_records(form, precision):
     plain = _solver(p, "stencil", bounds=lam, s=8)
     with pytest.raises(abi.SStepError):
         abi.sstep_cg_history(plain.h, 4)
+
+
+# Degenerate 3D grids with nx even (a line or a single plane): the register-blocked persistent
+# steps and residuals (7-point and 27-point) with ny = 1 or nz = 1, against the oracle's basis
+# and residual; the mixed form through TMA tiles (nx a multiple of 4) bitwise equal to plain
+# loads.
+DEGENERATE = [(6, 1, 3), (4, 5, 1), (8, 1, 1)]
+
+
+@pytest.mark.parametrize("dims", DEGENERATE, ids=["x".join(map(str, d)) for d in DEGENERATE])
+@pytest.mark.parametrize("stencil", ["star", "box"])
+def test_degenerate_even_grids_basis_and_residual(dims, stencil):
+    from paper_2512_09642_gb300 import SStepCG
+    p = W.make("deg", dims, config=47, stencil=stencil)
+    op = O.Operator(*p.csr())
+    lam = (0.03, 2.05)
+    s = 4
+    sv = SStepCG(grid=p.dims, stencil=stencil, bounds=lam, s=s)
+    P = sv.basis(_dev(p.b), s + 1).cpu().numpy()
+    ref = O.chebyshev_basis(op, p.b, s, lam[0], lam[1], ncols=s + 1)
+    for j in range(s + 1):
+        assert _rel(P[j], ref[:, j]) <= 1e-12, j
+    x = np.random.default_rng(3).uniform(-1, 1, p.n)
+    assert _rel(sv.apply(_dev(x)).cpu().numpy(), op.matvec(x)) <= 1e-14
+    sv2 = SStepCG(grid=p.dims, stencil=stencil, bounds=lam, s=2, tol=1e-30, max_outer=1)
+    xg, info = sv2.solve(_dev(p.b))
+    r_true = p.b - op.matvec(xg.cpu().numpy())
+    assert info["rel_res_true"] == pytest.approx(np.linalg.norm(r_true) / np.linalg.norm(p.b), rel=1e-10, abs=1e-14)
+
+
+@pytest.mark.parametrize("dims", [(4, 5, 1), (8, 1, 1)], ids=["4x5x1", "8x1x1"])
+def test_degenerate_grids_tma_step_equals_plain(dims):
+    from paper_2512_09642_gb300 import SStepCG
+    p = W.make("deg", dims, config=48)
+    xs = {}
+    for path in ("tma", "plain"):
+        sv = SStepCG(grid=p.dims, bounds=(0.03, 2.05), s=4, nu=10, tol=1e-30, max_outer=2, check_every=1,
+                     precision="mixed", gram_form="moments", step_kernel=path)
+        x, info = sv.solve(_dev(p.b))
+        assert info["step_tma"] == (path == "tma")
+        xs[path] = x.cpu().numpy()
+        sv.close()
+    assert np.array_equal(xs["tma"], xs["plain"])
