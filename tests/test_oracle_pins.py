@@ -90,6 +90,27 @@ def test_poisson_generator_structure(dims):
     assert np.all(rows[interior] == 0) and np.all(rows[~interior] > 0)
 
 
+@pytest.mark.parametrize("dims", [(6, 1, 3), (1, 5, 4), (1, 13, 1), (8, 1, 1), (4, 5, 1), (1, 7), (5, 1)])
+@pytest.mark.parametrize("diffusion", [False, True])
+def test_star_generator_on_grids_with_unit_extents(dims, diffusion):
+    """Grids with an axis of extent 1, where two axes share a stride (nx x 1 x nz: the y and z
+    strides are both nx): each row couples exactly the in-grid face neighbours by grid
+    coordinates, and the CSR agrees with the matrix-free form."""
+    kappa = W.lognormal_kappa(dims, 0.5, 81) if diffusion else None
+    op = O.Operator(*W.csr(dims, kappa))
+    A = _dense(op)
+    assert np.allclose(A, A.T, rtol=0, atol=1e-14)
+    nx, ny, nz = W.grid_shape(dims)
+    idx = np.arange(A.shape[0])
+    i, j, k = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    for r in range(A.shape[0]):
+        nb = [c for c in range(A.shape[0]) if abs(i[c] - i[r]) + abs(j[c] - j[r]) + abs(k[c] - k[r]) == 1]
+        off = [c for c in np.flatnonzero(A[r]) if c != r]
+        assert sorted(off) == sorted(nb), (r, off, nb)
+    x = rng.uniform(9, A.shape[0])
+    assert np.allclose(A @ x, W.apply(dims, x, kappa), rtol=0, atol=1e-12)
+
+
 @pytest.mark.parametrize("dims", [(8, 6), (4, 3, 5)])
 def test_jacobi_poisson_spectrum_closed_form(dims):
     """Eigenvalues of D^-1 A for the Dirichlet Laplacian: 1 - (1/d) sum_i cos(k_i pi / (N_i + 1))."""

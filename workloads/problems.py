@@ -77,8 +77,11 @@ def csr(dims, kappa: Optional[np.ndarray] = None, index_dtype=np.int32):
     axes = _axes(dims)
     d = len(axes)
     nslots = 2 * d + 1
-    # neighbour offsets in ascending order: -stride(last) ... -1, 0, +1 ... +stride(last)
-    offs = [-a[0] for a in reversed(axes)] + [0] + [a[0] for a in axes]
+    # (offset, axis) per slot in ascending order of the offset: -stride(last) ... -1, 0, +1 ...
+    # +stride(last); the axis is carried with the slot (two axes share a stride when one of them
+    # has extent 1, e.g. the y and z strides of an nx x 1 x nz grid)
+    slots = [(-a[0], ax) for ax, a in reversed(list(enumerate(axes)))] + [(0, None)] + \
+            [(a[0], ax) for ax, a in enumerate(axes)]
     counts = np.empty(n, dtype=np.int64)
     plane = nx * ny
     slab = max(1, (1 << 22) // plane)
@@ -92,10 +95,9 @@ def csr(dims, kappa: Optional[np.ndarray] = None, index_dtype=np.int32):
         valid = np.zeros((idx.size, nslots), dtype=bool)
         diag = np.zeros(idx.size, dtype=np.float64)
         kc = None if kappa is None else kappa[idx]
-        for slot, off in enumerate(offs):
+        for slot, (off, ax) in enumerate(slots):
             if off == 0:
                 continue
-            ax = [a[0] for a in axes].index(abs(off))
             ext = axes[ax][1]
             inside = (coord[ax] > 0) if off < 0 else (coord[ax] < ext - 1)
             nb = idx + off
