@@ -308,6 +308,22 @@ def test_full_size_poisson3d_256_first_five_iterates(form):
         sv2.close()
 
 
+@pytest.mark.slow
+def test_full_size_poisson3d_256_mixed_tma_first_iterates():
+    """The mixed form at 256^3 as the benchmark runs it (fused moments, refresh every 8): its
+    FP32 steps go through TMA tiles (the three FP32 vectors exceed L2), and x_1, x_3 agree with
+    the FP64 oracle's to FP32 level."""
+    p, lam, ref = _oracle_256()
+    b = _dev(p.b)
+    for k, tol in ((1, 1e-5), (3, 1e-4)):
+        sv = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-30, max_outer=k, check_every=1,
+                     precision="mixed", gram_form="fused", refresh_period=8)
+        x, info = sv.solve(b)
+        assert info["outer_iters"] == k and info["step_tma"] == 1
+        assert _rel(x.cpu().numpy(), ref.history[k - 1].x) <= tol, (k, _rel(x.cpu().numpy(), ref.history[k - 1].x))
+        sv.close()
+
+
 def test_fused_form_reaches_tolerance_like_oracle_and_graph_equals_host_loop():
     """Full solves with the fused moments (FP64) on a 2D and a 3D Poisson problem: true
     residual <= 1e-8, outer count within one of the oracle's, the solution within 1e-7; the
