@@ -637,7 +637,9 @@ def run_ours(args):
                        "model_bytes_per_outer": ob * n,
                        "ms_per_outer": r["t"] / max(outers, 1) * 1e3,
                        "e2e_s": r["e2e"], "roofline": roof, "kernels": table, "clocks": r["clocks"],
-                       "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"]))}
+                       "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"])),
+                       # the mixed forms' FP32 step: through TMA tiles or plain loads (opts.step_kernel AUTO)
+                       "fp32_step": ("tma" if info.get("step_tma") else "plain") if prec.startswith("mixed") else None}
         res[prec] = r
     # speedups and differences are against the first FP64 form listed (the headline, FP64
     # with the moments Gram, by default)
@@ -906,7 +908,9 @@ def run_sweep(args):
                          "kernels": {k: {f: v[f] for f in ("avg_launch_ms", "share", "hbm_gbs", "fp64_gops")}
                                      for k, v in table.items() if v["avg_launch_ms"]},
                          "clocks": r["clocks"],
-                         "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"]))})
+                         "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"])),
+                       # the mixed forms' FP32 step: through TMA tiles or plain loads (opts.step_kernel AUTO)
+                       "fp32_step": ("tma" if info.get("step_tma") else "plain") if prec.startswith("mixed") else None})
             torch.cuda.empty_cache()
     if rank == 0:
         head = next(rw for rw in rows if rw["s"] == 8 and rw["form"] == "fp64+mom")
