@@ -116,7 +116,9 @@ typedef struct {
                               tensor-map (TMA) tiles when the step's three vectors exceed the L2
                               cache, else plain loads; SSTEP_STEP_TMA / SSTEP_STEP_PLAIN force one
                               (TMA falls back to plain loads where the shape does not allow it).
-                              Both give bitwise the same basis. Elsewhere: unused */
+                              Both give the same basis bit for bit; with FUSED the moments'
+                              per-block partial sums follow each kernel's blocks, so the solves
+                              agree to FP32 rounding. Elsewhere: unused */
 } sstep_cg_opts;
 
 typedef struct {
@@ -352,7 +354,8 @@ SSTEP_API sstep_status sstep_gram_fgs_noalloc(int64_t n, int s, int nu, int gram
  * control block's termination state afterwards: 4 (timed out) is the designed outcome, and
  * the CUDA context stays usable. Returns SSTEP_ERR_UNSUPPORTED when the driver has no
  * tensor-map encoder, SSTEP_ERR_CUDA when a CUDA call failed, SSTEP_ERR_INVALID_ARG for a
- * null pointer. Allocates and frees its own 64 KB on the current device (synchronous). */
+ * null pointer. Allocates and frees its own 8 KB and control block on the current device
+ * (synchronous). */
 SSTEP_API sstep_status sstep_selftest_tma_timeout(int* done_state);
 
 #ifdef __cplusplus
