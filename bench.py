@@ -910,7 +910,8 @@ def run_sweep(args):
                          "clocks": r["clocks"],
                          "gpu_launches": int(sum(i["kernel_launches"] for i in r["infos"])),
                        # the mixed forms' FP32 step: through TMA tiles or plain loads (opts.step_kernel AUTO)
-                       "fp32_step": ("tma" if info.get("step_tma") else "plain") if prec.startswith("mixed") else None})
+                       "fp32_step": (("tma" if r["infos"][-1].get("step_tma") else "plain")
+                                     if prec.startswith("mixed") else None)})
             torch.cuda.empty_cache()
     if rank == 0:
         head = next(rw for rw in rows if rw["s"] == 8 and rw["form"] == "fp64+mom")
