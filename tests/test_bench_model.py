@@ -92,3 +92,47 @@ def test_fused_csr_and_refresh_models():
     assert cm["cheb_step"] == {"ops": 0, "bytes": 8 * 7.0 + 4 + 12 + 4}
     assert bench.form_gram("mixed+fused+r8") == "fused" and bench.form_refresh("mixed+fused+r8") == 8
     assert bench.form_gram("fp64+mom") == "moments" and bench.form_refresh("fp64") == 1
+
+
+def test_kernel_report_dominant_kernel_and_roof():
+    """The line's roofline comes from the kernel with the largest share of solve time: its
+    average sampled launch time times its launches per solve (s steps, one Gram and one update
+    per outer iteration, the residuals at start, exit and each refresh). The FP64 step is
+    measured against the FP64 FMA rate, the mixed form's FP32 step against the HBM rate."""
+    import types
+    args = types.SimpleNamespace(s=8)
+    n = 256 ** 3
+
+    def info(ms, launches, outers=170, refreshes=0):
+        return {"prof_ms": list(ms), "prof_launches": list(launches), "outer_iters": outers,
+                "refreshes": refreshes}
+
+    # FP64 moments: 8 step launches at 0.2 ms, one Gram at 0.3 ms, one update at 0.4 ms,
+    # residual 0.5 ms; two sampled solves with the same averages
+    infos = [info([1.6, 0.3, 0.4, 0.5], [8, 1, 1, 1]), info([3.2, 0.6, 0.8, 1.0], [16, 2, 2, 2])]
+    roof, table = bench.kernel_report(args, n, infos, "fp64+mom")
+    assert abs(table["cheb_step"]["avg_launch_ms"] - 0.2) < 1e-15
+    assert table["cheb_step"]["launches_per_solve"] == 8 * 170
+    assert table["gram_fgs"]["launches_per_solve"] == table["update"]["launches_per_solve"] == 170
+    assert table["residual"]["launches_per_solve"] == 2
+    assert abs(sum(v["share"] for v in table.values()) - 1.0) < 1e-12
+    assert roof["kernel"] == "cheb_step" and roof["bound"] == "alu"
+    ops = 7 * n
+    assert roof["fp64_ops_per_launch"] == ops and roof["bytes_per_launch"] == 24 * n
+    assert abs(roof["frac"] - ops / 0.2e-3 / bench.FP64_OPS_PEAK) < 1e-9
+    assert abs(roof["hbm_frac"] * bench.measured_peaks()[0] * 1e9 - 24 * n / 0.2e-3) < 1e-3 * 24 * n / 0.2e-3
+
+    # mixed, fused, refresh every 8: no FP64 work in the FP32 step, so its roof is HBM; the
+    # refreshes add one residual per group of 8 outer iterations
+    infos = [info([0.32, 0.05, 0.06, 0.09], [8, 1, 1, 1], outers=262, refreshes=1)]
+    roof, table = bench.kernel_report(args, n, infos, "mixed+fused+r8")
+    assert table["residual"]["launches_per_solve"] == -(-262 // 8) + 1 + 2 + 1
+    assert roof["kernel"] == "cheb_step" and roof["bound"] == "hbm"
+    by = bench.kernel_model(8, mixed=True, fused=True, write_r=True)["cheb_step"]["bytes"] * n
+    assert abs(roof["achieved"] - by / 0.04e-3 / 1e9) < 1e-6 * by / 0.04e-3 / 1e9
+    assert roof["peak"] == bench.measured_peaks()[0]
+
+    # a kernel never sampled has no time and no share
+    infos = [info([1.6, 0.3, 0.4, 0.0], [8, 1, 1, 0])]
+    roof, table = bench.kernel_report(args, n, infos, "fp64+mom")
+    assert table["residual"]["avg_launch_ms"] is None and table["residual"]["share"] == 0.0
