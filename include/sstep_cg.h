@@ -159,8 +159,9 @@ SSTEP_API sstep_status sstep_cg_create_csr(sstep_cg_t* handle, int64_t n, const 
  * dim = 2 (nz must be 1) or 3. kappa_d = NULL: the unscaled Poisson stencil, diagonal 2*dim
  * and -1 per in-grid neighbour (5- or 7-point). kappa_d = double[n] > 0: cell-centred
  * diffusion -div(kappa grad u); an interior face between cells a, b has weight
- * 2 ka kb / (ka + kb), a boundary face adds 2 kappa_cell to the diagonal.
- * Synchronises `stream`. */
+ * 2 ka kb / (ka + kb), a boundary face adds 2 kappa_cell to the diagonal. Grid extents:
+ * nx, ny, nz >= 1, ny <= 524280 and, in 3D, nz <= 524280; anything else gives
+ * SSTEP_ERR_INVALID_ARG before any CUDA call. Synchronises `stream`. */
 SSTEP_API sstep_status sstep_cg_create_stencil(sstep_cg_t* handle, int dim, int nx, int ny, int nz,
                                      const double* kappa_d, const sstep_cg_opts* opts,
                                      void* stream);
@@ -173,7 +174,9 @@ SSTEP_API sstep_status sstep_cg_create_stencil(sstep_cg_t* handle, int dim, int 
  * nor the relative residual); in 2D the 9-point one. dim = 2 (nz must be 1) or 3. M = D is
  * the constant 3^dim - 1, so the moments Gram form applies. The Gershgorin bound of D^-1 A
  * is 2, well above the spectrum's end near 36/26 in 3D; the paper's Lanczos-10 bounds
- * (bounds_mode LANCZOS10) are tighter. Synchronises `stream`. */
+ * (bounds_mode LANCZOS10) are tighter. Grid extents: nx, ny, nz >= 1, ny <= 524280 and, in
+ * 3D, nz <= 1048560; anything else gives SSTEP_ERR_INVALID_ARG before any CUDA call.
+ * Synchronises `stream`. */
 SSTEP_API sstep_status sstep_cg_create_box_stencil(sstep_cg_t* handle, int dim, int nx, int ny, int nz,
                                                    const sstep_cg_opts* opts, void* stream);
 

@@ -874,7 +874,9 @@ sstep_status sstep_cg_create_stencil(sstep_cg_t* out, int dim, int nx, int ny, i
     sstep_cg_t h = nullptr;
     sstep_status st = begin_create(out, opts, stream, &h);
     if (st != SSTEP_OK) return fail_create(h, st);
-    if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || nz < 1 || (dim == 2 && nz != 1) || ny > 65535 * 8) {
+    // ny and nz bound the grid's y and z extents at 8 rows and 8 planes per block
+    if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || nz < 1 || (dim == 2 && nz != 1) || ny > 65535 * 8 ||
+        (dim == 3 && nz > 65535 * 8)) {
         set_err(h, "bad grid: dim %d, %d x %d x %d", dim, nx, ny, nz);
         return fail_create(h, SSTEP_ERR_INVALID_ARG);
     }

@@ -95,6 +95,20 @@ def test_invalid_grid_rejected_on_host(abi, grid):
     assert ei.value.status == 1
 
 
+@pytest.mark.parametrize("create,grid", [("stencil", (3, 4, 524281, 4)), ("stencil", (2, 4, 524281, 1)),
+                                         ("stencil", (3, 4, 4, 524281)), ("box", (3, 4, 524281, 4)),
+                                         ("box", (3, 4, 4, 1048561))])
+def test_grid_extents_beyond_launch_limits_rejected_on_host(abi, create, grid):
+    """A stencil grid whose y or z extent would need more than 65535 blocks of 8 rows or 8
+    planes (16 for the box stencil's z) is refused at create, before any CUDA call."""
+    with pytest.raises(abi.SStepError) as ei:
+        if create == "stencil":
+            abi.sstep_cg_create_stencil(*grid, None, abi.sstep_cg_default_opts(), stream=0)
+        else:
+            abi.sstep_cg_create_box_stencil(*grid, abi.sstep_cg_default_opts(), stream=0)
+    assert ei.value.status == 1 and "bad grid" in abi.sstep_cg_last_error(None)
+
+
 def test_block_conjugate_options_checked_on_host(abi):
     with pytest.raises(abi.SStepError) as ei:
         abi.sstep_cg_create_stencil(2, 8, 8, 1, None, abi.sstep_cg_default_opts(block_conjugate=2), stream=0)
