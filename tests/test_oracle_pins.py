@@ -422,6 +422,45 @@ def test_s1_is_steepest_descent():
         assert np.linalg.norm(res.history[k].x - x) <= 1e-13 * np.linalg.norm(x)
 
 
+def test_minv_r_start_s1_is_preconditioned_steepest_descent():
+    """The alternative start p_0 = M^-1 r_k at s = 1: x += a z with z = M^-1 r and
+    a = z^T r / z^T A z, the Jacobi-preconditioned steepest descent step (textbook)."""
+    p = W.make("t", (10, 8), kappa_sigma=0.7, config=9)
+    op = O.Operator(*p.csr())
+    res = O.solve(op, p.b, s=1, nu=1, lam_min=0.1, lam_max=2.0, tol=1e-30, max_outer=4, history=4,
+                  basis_start="minv_r")
+    A = _dense(op)
+    minv = 1.0 / np.diag(A)
+    x = np.zeros(op.n)
+    for k in range(4):
+        r = p.b - A @ x
+        z = minv * r
+        x = x + (z @ r) / (z @ (A @ z)) * z
+        assert np.linalg.norm(res.history[k].x - x) <= 1e-13 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("dims", [(9, 7), (6, 5, 4)])
+def test_minv_r_start_equals_r_start_for_constant_preconditioner(dims):
+    """With a constant M = m I (Jacobi on the Poisson stencil, m = 2d) the start M^-1 r_k
+    scales the basis by 1/m; the column scaling takes that factor out of G and c, so alpha
+    grows by m and x_k, r_k are those of the p_0 = r_k start of Section 2. With a varying
+    diagonal (diffusion) the two starts give different iterates."""
+    p = W.make("t", dims, config=9)
+    op = O.Operator(*p.csr())
+    kw = dict(s=4, nu=20, lam_min=0.05, lam_max=2.0, tol=1e-30, max_outer=5, history=5)
+    a = O.solve(op, p.b, **kw)
+    b = O.solve(op, p.b, basis_start="minv_r", **kw)
+    for ha, hb in zip(a.history, b.history):
+        assert np.linalg.norm(ha.x - hb.x) <= 1e-12 * np.linalg.norm(ha.x)
+        assert np.linalg.norm(ha.r - hb.r) <= 1e-11 * np.linalg.norm(ha.r)
+        assert np.allclose(hb.alpha, 2 * len(dims) * ha.alpha, rtol=1e-10, atol=0)
+    q = W.make("t", dims, kappa_sigma=1.0, config=9)
+    opq = O.Operator(*q.csr())
+    a = O.solve(opq, q.b, **kw)
+    b = O.solve(opq, q.b, basis_start="minv_r", **kw)
+    assert np.linalg.norm(a.history[0].x - b.history[0].x) > 1e-3 * np.linalg.norm(a.history[0].x)
+
+
 def test_tiny_system_one_outer_with_cholesky_is_exact():
     n = 5
     M = rng.uniform(31, n * n).reshape(n, n)
