@@ -606,9 +606,10 @@ sstep_status collect_outer_profile(sstep_cg_t h, sstep_cg_info* inf, bool refres
 }
 
 sstep_status ensure_events(sstep_cg_t h) {
-    if (h->ev[0]) return SSTEP_OK;
-    for (int i = 0; i < SSTEP_MAX_S + 4; ++i) CK(cudaEventCreate(&h->ev[i]));
-    CK(cudaEventCreate(&h->rev[0]));
+    if (h->rev[1]) return SSTEP_OK;   // the last one created: all exist
+    for (int i = 0; i < SSTEP_MAX_S + 4; ++i)
+        if (!h->ev[i]) CK(cudaEventCreate(&h->ev[i]));
+    if (!h->rev[0]) CK(cudaEventCreate(&h->rev[0]));
     CK(cudaEventCreate(&h->rev[1]));
     return SSTEP_OK;
 }
@@ -685,10 +686,10 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
     sstep_cg_info inf{};
     inf.lambda_min_used = h->lmin;
     inf.lambda_max_used = h->lmax;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventRecord(e0, h->stream));
+    SolveEvents tev;
+    CK(cudaEventCreate(&tev.e0));
+    CK(cudaEventCreate(&tev.e1));
+    CK(cudaEventRecord(tev.e0, h->stream));
     // control block: running, zero outers, tolerance
     Ctl init{};
     init.tol_sq = h->opts.tol * h->opts.tol;
@@ -772,12 +773,10 @@ sstep_status solve_impl(sstep_cg_t h, const double* b, double* x, sstep_cg_info*
         else if (done == MAX_OUTER || !true_ok) status = SSTEP_ERR_NO_CONVERGENCE;
         break;
     }
-    CK(cudaEventRecord(e1, h->stream));
-    CK(cudaEventSynchronize(e1));
+    CK(cudaEventRecord(tev.e1, h->stream));
+    CK(cudaEventSynchronize(tev.e1));
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    CK(cudaEventElapsedTime(&ms, tev.e0, tev.e1));
     const Ctl& c = *h->ctl_h;
     inf.outer_iters = c.outer;
     inf.refreshes = refreshes;
@@ -992,22 +991,20 @@ sstep_status sstep_cg_solve_host(sstep_cg_t h, const double* b_h, double* x_h, s
     if (!h->bx_dev) CK(cudaMalloc(&h->bx_dev, sizeof(double) * 2 * ((n + 31) / 32 * 32)));
     double* bd = h->bx_dev;
     double* xd = h->bx_dev + (n + 31) / 32 * 32;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventRecord(e0, h->stream));
+    SolveEvents tev;
+    CK(cudaEventCreate(&tev.e0));
+    CK(cudaEventCreate(&tev.e1));
+    CK(cudaEventRecord(tev.e0, h->stream));
     CK(cudaMemcpyAsync(bd, b_h, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(xd, x_h, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
     sstep_cg_info inf{};
     sstep_status st = solve_impl(h, bd, xd, &inf);
     if (st != SSTEP_OK && st != SSTEP_ERR_NO_CONVERGENCE && st != SSTEP_ERR_NUMERICAL) return st;
     CK(cudaMemcpyAsync(x_h, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaEventRecord(e1, h->stream));
-    CK(cudaEventSynchronize(e1));
+    CK(cudaEventRecord(tev.e1, h->stream));
+    CK(cudaEventSynchronize(tev.e1));
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    CK(cudaEventElapsedTime(&ms, tev.e0, tev.e1));
     inf.ms = ms;
     if (info) *info = inf;
     return st;
@@ -1015,7 +1012,7 @@ sstep_status sstep_cg_solve_host(sstep_cg_t h, const double* b_h, double* x_h, s
 
 sstep_status sstep_cg_destroy(sstep_cg_t h) {
     if (!h) return SSTEP_OK;
-    if (h->stream || true) cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->stream);
     cudaFree(h->diag);
     cudaFree(h->cdinv);
     cudaFree(h->faces);

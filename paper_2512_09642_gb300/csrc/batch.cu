@@ -334,10 +334,10 @@ sstep_status sstep_cg_batch_solve(sstep_cg_batch_t h, const double* b_d, double*
     cudaStream_t st = h->stream;
     const int count = h->count;
     const BatchDev B = dev_view(h);
-    cudaEvent_t e0, e1;
-    BCK(cudaEventCreate(&e0));
-    BCK(cudaEventCreate(&e1));
-    BCK(cudaEventRecord(e0, st));
+    SolveEvents tev;
+    BCK(cudaEventCreate(&tev.e0));
+    BCK(cudaEventCreate(&tev.e1));
+    BCK(cudaEventRecord(tev.e0, st));
     BCK(launch_batch_init(B, h->opts.tol * h->opts.tol, h->opts.max_outer, st));
     BCK(launch_batch_residual(B, b_d, x_d, h->P, 0, st));
     std::vector<int> refreshes(count, 0);
@@ -388,12 +388,10 @@ sstep_status sstep_cg_batch_solve(sstep_cg_batch_t h, const double* b_d, double*
         BCK(cudaMemcpyAsync(h->running, &restart, sizeof(int), cudaMemcpyHostToDevice, st));
         BCK(cudaStreamSynchronize(st));
     }
-    BCK(cudaEventRecord(e1, st));
-    BCK(cudaEventSynchronize(e1));
+    BCK(cudaEventRecord(tev.e1, st));
+    BCK(cudaEventSynchronize(tev.e1));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaEventElapsedTime(&ms, tev.e0, tev.e1);
     sstep_status overall = SSTEP_OK;
     int max_outer = 0, n_ok = 0;
     double worst = 0.0;

@@ -7,6 +7,18 @@
 
 namespace sstep {
 
+// The two events that time one solve, destroyed on every return path of the solve.
+struct SolveEvents {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SolveEvents() = default;
+    SolveEvents(const SolveEvents&) = delete;
+    SolveEvents& operator=(const SolveEvents&) = delete;
+    ~SolveEvents() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 // Operator description handed to kernels (plain pointers, no ownership).
 struct OpDesc {
     int kind;            // OP_CSR or OP_STENCIL
