@@ -277,7 +277,7 @@ enum { SSTEP_COARSE_FORMED = 0, SSTEP_COARSE_STREAMING = 1 };
  *     n_c^2 doubles allocated for the call) and swept;
  *   mode SSTEP_COARSE_STREAMING: A_c is never formed (Section 6's streaming form): P y is kept
  *     on the fine grid and row i of A_c y is the sum of A_f (P y) over aggregate i; memory
- *     O(n_f + n_c).
+ *     O(n_f + n_c), n_c < 2^31.
  * g_d (double[n_c]) and y_d (double[n_c], in: y^(0), out: y^(nu)) are device arrays; the
  * handle's residual scratch is used. Synchronises the handle's stream. */
 SSTEP_API sstep_status sstep_coarse_fgs(sstep_cg_t handle, int bx, int by, int bz, const double* g_d, double* y_d,

@@ -953,6 +953,10 @@ sstep_status sstep_coarse_fgs(sstep_cg_t h, int bx, int by, int bz, const double
         return SSTEP_ERR_INVALID_ARG;
     }
     const int64_t nc = (int64_t)((h->op.nx + bx - 1) / bx) * ((h->op.ny + by - 1) / by) * ((h->op.nz + bz - 1) / bz);
+    if (nc > 2147483647LL) {
+        set_err(h, "coarse FGS: n_c = %lld aggregates, above 2^31 - 1", (long long)nc);
+        return SSTEP_ERR_INVALID_ARG;
+    }
     if (mode == SSTEP_COARSE_FORMED && nc > coarse_formed_max_nc()) {
         set_err(h, "coarse FGS: formed A_c limited to n_c <= %d (got %lld); use the streaming mode",
                 coarse_formed_max_nc(), (long long)nc);
