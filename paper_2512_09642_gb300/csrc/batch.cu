@@ -170,7 +170,8 @@ sstep_status sstep_cg_batch_create(sstep_cg_batch_t* out, int count, const int* 
     if (opts) o = *opts; else sstep_cg_default_opts(&o);
     if (count < 1 || !grids_h) { berr(h, "count must be >= 1 with a grid per system"); return fail(SSTEP_ERR_INVALID_ARG); }
     if (o.s < 1 || o.s > 16) { berr(h, "batched form: s = %d outside [1, 16]", o.s); return fail(SSTEP_ERR_INVALID_ARG); }
-    if (o.nu < 1 || o.nu > 10000 || !(o.tol > 0.0) || o.max_outer < 0 || o.max_refresh < 0 || o.check_every < 1) {
+    if (o.nu < 1 || o.nu > 10000 || !(o.tol > 0.0) || !std::isfinite(o.tol) || o.max_outer < 0 || o.max_refresh < 0 ||
+        o.check_every < 1) {
         berr(h, "invalid nu, tol, max_outer, max_refresh or check_every");
         return fail(SSTEP_ERR_INVALID_ARG);
     }
@@ -184,8 +185,14 @@ sstep_status sstep_cg_batch_create(sstep_cg_batch_t* out, int count, const int* 
         berr(h, "batched form: Jacobi, FP64 and p_0 = r only");
         return fail(SSTEP_ERR_UNSUPPORTED);
     }
-    if (o.bounds_mode == SSTEP_BOUNDS_GIVEN && !(o.lambda_max > o.lambda_min && o.lambda_min >= 0.0)) {
+    if (o.bounds_mode == SSTEP_BOUNDS_GIVEN && !(o.lambda_max > o.lambda_min && o.lambda_min >= 0.0 &&
+                                                 std::isfinite(o.lambda_max))) {
         berr(h, "need 0 <= lambda_min < lambda_max");
+        return fail(SSTEP_ERR_INVALID_ARG);
+    }
+    if (o.bounds_mode != SSTEP_BOUNDS_GIVEN && o.bounds_mode != SSTEP_BOUNDS_GERSH_LANCZOS10 &&
+        o.bounds_mode != SSTEP_BOUNDS_LANCZOS10) {
+        berr(h, "unknown bounds_mode %d", o.bounds_mode);
         return fail(SSTEP_ERR_INVALID_ARG);
     }
     if (o.batch_chunk < 0 || (o.batch_chunk > 0 && o.batch_chunk < 256) || o.batch_ctas_per_sm < 0 ||

@@ -175,3 +175,28 @@ def test_noalloc_arguments_checked_on_host(abi):
             assert "16" in msg
     # mdiag given: mconst is not used
     assert call(md=md, mc=0.0, s=17) == 1
+
+
+@pytest.mark.parametrize("grids,bad,status", [
+    ([], {}, 1),                                                   # no systems
+    ([(8, 8)], dict(s=17), 1), ([(8, 8)], dict(s=0), 1), ([(8, 8)], dict(nu=0), 1),
+    ([(8, 8)], dict(tol=0.0), 1), ([(8, 8)], dict(tol=float("inf")), 1),
+    ([(8, 8)], dict(max_outer=-1), 1), ([(8, 8)], dict(check_every=0), 1),
+    ([(8, 8)], dict(gram_solver=5), 1),
+    ([(8, 8)], dict(bounds_mode=0, lambda_min=1.0, lambda_max=0.5), 1),
+    ([(8, 8)], dict(bounds_mode=0, lambda_min=0.1, lambda_max=float("inf")), 1),
+    ([(8, 8)], dict(bounds_mode=7), 1),
+    ([(8, 8)], dict(batch_chunk=100), 1), ([(8, 8)], dict(batch_ctas_per_sm=9), 1),
+    ([(8, 8), (0, 8)], {}, 1), ([(8, 8, 0)], {}, 1),              # an empty grid
+    ([(8, 8)], dict(precision=1), 7), ([(8, 8)], dict(precond=0), 7),   # FP64 Jacobi only
+    ([(8, 8)], dict(gram_form=2), 7), ([(8, 8)], dict(block_conjugate=1), 7),
+])
+def test_batch_create_checked_on_host(abi, grids, bad, status):
+    """The batched form's options and grids are checked before its first CUDA call:
+    INVALID_ARG (1) for values outside their ranges, UNSUPPORTED (7) for the forms it does not
+    run (mixed precision, no preconditioner, the fused Gram, block conjugation)."""
+    o = abi.sstep_cg_default_opts(**bad)
+    with pytest.raises(abi.SStepError) as ei:
+        abi.sstep_cg_batch_create(grids, [None] * len(grids), o, stream=0)
+    assert ei.value.status == status, str(ei.value)
+    assert str(ei.value).split(": ", 1)[1]
