@@ -200,3 +200,28 @@ def test_batch_create_checked_on_host(abi, grids, bad, status):
         abi.sstep_cg_batch_create(grids, [None] * len(grids), o, stream=0)
     assert ei.value.status == status, str(ei.value)
     assert str(ei.value).split(": ", 1)[1]
+
+
+def test_solver_refuses_arrays_the_abi_cannot_check():
+    """The C ABI takes plain pointers whose lengths the handle implies, so SStepCG refuses, before
+    any call, a tensor that is not on the GPU, has another element type, another number of
+    elements or lives on another device (stand-in objects with the tensor attributes it reads)."""
+    import torch
+    from paper_2512_09642_gb300.solver import check_array
+
+    class Fake:
+        def __init__(self, dtype=torch.float64, n=10, dev="cuda:0", cuda=True):
+            self.dtype, self._n, self.device, self.is_cuda = dtype, n, torch.device(dev), cuda
+
+        def numel(self):
+            return self._n
+
+    dev = torch.device("cuda", 0)
+    check_array(Fake(), "b", 10, torch.float64, dev)
+    check_array(Fake(torch.int32, 11), "rowptr", 11, torch.int32, dev)
+    for bad, what in ((Fake(cuda=False, dev="cpu"), "CUDA"), (Fake(torch.float32), "float64"),
+                      (Fake(n=9), "10 elements"), (Fake(dev="cuda:1"), "cuda:0")):
+        with pytest.raises(ValueError, match=what):
+            check_array(bad, "b", 10, torch.float64, dev)
+    with pytest.raises(ValueError, match="CUDA"):
+        check_array(torch.zeros(10, dtype=torch.float64), "b", 10, torch.float64, dev)
