@@ -225,3 +225,21 @@ def test_solver_refuses_arrays_the_abi_cannot_check():
             check_array(bad, "b", 10, torch.float64, dev)
     with pytest.raises(ValueError, match="CUDA"):
         check_array(torch.zeros(10, dtype=torch.float64), "b", 10, torch.float64, dev)
+
+
+def test_microbenchmarks_compile(tmp_path):
+    """The standalone programs behind the FP64 roof and the one-warp latency figures keep
+    compiling for sm_103a against the library's current headers (no GPU needed)."""
+    import glob
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    srcs = sorted(glob.glob(os.path.join(ROOT, "paper_2512_09642_gb300", "microbench", "*.cu")))
+    assert {os.path.basename(s) for s in srcs} >= {"fp64_rate.cu", "warp_fp64_latency.cu", "fgs_sweep_forms.cu"}
+    for src in srcs:
+        r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                            "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include"), "-c", src,
+                            "-o", str(tmp_path / (os.path.basename(src) + ".o"))], capture_output=True, text=True)
+        assert r.returncode == 0, (src, r.stderr[-2000:])
