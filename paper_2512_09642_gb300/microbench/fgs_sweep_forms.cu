@@ -3,8 +3,8 @@
 // step timed in one warp. Standalone; not part of the library.
 // Build and run from the repository root:
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -std=c++17 --expt-relaxed-constexpr -Iinclude \
-//        -o fgs_sweep_forms paper_2512_09642_gb300/microbench/fgs_sweep_forms.cu
-//   ./fgs_sweep_forms
+//        -o /tmp/fgs_sweep_forms paper_2512_09642_gb300/microbench/fgs_sweep_forms.cu
+//   /tmp/fgs_sweep_forms
 #include <cstdio>
 #include <cstdlib>
 #include <cmath>

@@ -2,8 +2,8 @@
 // independent FMA/ADD/MUL chains per thread at full occupancy, operands loaded from memory
 // (random non-zero or zero), CUDA-event timing. Standalone; not part of the library.
 // Build and run from the repository root:
-//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o fp64_rate paper_2512_09642_gb300/microbench/fp64_rate.cu
-//   ./fp64_rate
+//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/fp64_rate paper_2512_09642_gb300/microbench/fp64_rate.cu
+//   /tmp/fp64_rate
 #include <cstdio>
 #include <cstdlib>
 #include <cstdint>

@@ -4,8 +4,8 @@
 // compares it with the current one) against single-thread sequential forms; also the
 // globaltimer rate against CUDA events. Standalone; not part of the library.
 // Build and run from the repository root:
-//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o warp_fp64_latency paper_2512_09642_gb300/microbench/warp_fp64_latency.cu
-//   ./warp_fp64_latency
+//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/warp_fp64_latency paper_2512_09642_gb300/microbench/warp_fp64_latency.cu
+//   /tmp/warp_fp64_latency
 #include <cstdio>
 #include <cstdlib>
 #include <cmath>
