@@ -95,7 +95,10 @@ typedef struct {
     int max_refresh;       /* true-residual restarts after recursive convergence (default 3) */
     uint64_t seed;         /* splitmix64 stream of the Lanczos start vector (default 5000) */
     int use_graph;         /* 1: run the outer loop as a CUDA graph with a device-side while
-                              condition; 0: host loop that checks every check_every outers */
+                              condition; 0: host loop that checks every check_every outers. The
+                              handle keeps the graph of the last (b, x) pointer pair it solved;
+                              a call with another pair captures and instantiates it again (host
+                              time), so repeated solves should reuse their b and x buffers */
     int check_every;       /* host loop only: outers launched between convergence checks */
     int profile_every;     /* > 0: time each kernel of one outer iteration in every this many
                               check intervals with CUDA events (sstep_cg_info.prof_*); 0: off */

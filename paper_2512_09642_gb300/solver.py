@@ -78,7 +78,9 @@ class SStepCG:
         return self.opts.s
 
     def solve(self, b: torch.Tensor, x0: Optional[torch.Tensor] = None, allow_no_convergence: bool = True):
-        """Returns (x, info dict); x0 defaults to zeros."""
+        """Returns (x, info dict); x0 defaults to zeros. x is a new tensor: with use_graph the
+        handle captures its outer-loop graph again for each new (b, x) pair, so loops of solves
+        that want the graph reused call solve_into with the same buffers."""
         self._vec(b, "b")
         x = torch.zeros_like(b) if x0 is None else self._vec(x0, "x0").clone()
         info = abi.sstep_cg_solve(self.h, b, x, allow=(5,) if allow_no_convergence else ())
