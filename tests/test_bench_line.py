@@ -1,0 +1,132 @@
+"""bench.py's JSON line on the CPU: run_ours on a small 3D Poisson grid with the CUDA calls and the
+library's solve replaced by stand-ins (fixed event times, fixed solve records), so that the
+line's keys and their arithmetic (value, ms_per_step, e2e bytes, roofline, launch count,
+speedups) are checked without a GPU. The CPU baseline leg runs the oracle for real."""
+import json
+import os
+import sys
+
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+SIDE, STEPS, WARMUP = 8, 2, 1
+EVENT_MS = 1500.0        # every timed region: 1.5 s over STEPS solves
+OUTERS, LAUNCHES = 12, 150
+
+
+@pytest.fixture
+def fake_gpu(monkeypatch):
+    import paper_2512_09642_gb300 as pkg
+    from paper_2512_09642_gb300 import abi
+
+    class Event:
+        def __init__(self, **kw):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return EVENT_MS
+
+    zeros = torch.zeros
+    monkeypatch.setattr(torch.cuda, "Event", Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a, **k: None)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch, "zeros", lambda *a, device=None, **k: zeros(*a, **k))
+
+    calls = {"device": [], "host": 0}
+
+    class Info:
+        def __init__(self, mixed):
+            self.mixed = mixed
+
+        def as_dict(self):
+            return {"outer_iters": OUTERS, "status": "SSTEP_OK", "rel_res_true": 5e-9, "kernel_launches": LAUNCHES,
+                    "prof_ms": [0.8, 0.3, 0.2, 0.1], "prof_launches": [8, 1, 1, 1], "refreshes": 0,
+                    "step_tma": 1 if self.mixed else 0, "ms": EVENT_MS / STEPS}
+
+    class Solver:
+        def __init__(self, **kw):
+            self.h = object()
+            self.mixed = kw.get("precision") == "mixed"
+
+        def close(self):
+            pass
+
+    handles = {}
+
+    def make(**kw):
+        sv = Solver(**kw)
+        handles[id(sv.h)] = sv
+        return sv
+
+    def solve(h, b, x, allow=(5,)):
+        calls["device"].append(x.data_ptr())
+        x.copy_(b)
+        return Info(handles[id(h)].mixed)
+
+    def solve_host(h, b, x, allow=(5,)):
+        calls["host"] += 1
+        return Info(handles[id(h)].mixed)
+
+    monkeypatch.setattr(pkg, "SStepCG", make, raising=False)
+    monkeypatch.setattr(abi, "sstep_cg_solve", solve)
+    monkeypatch.setattr(abi, "sstep_cg_solve_host", solve_host)
+    return calls
+
+
+def test_bench_line_carries_every_contract_key(fake_gpu, monkeypatch, capsys):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--side", str(SIDE), "--steps", str(STEPS), "--warmup",
+                                      str(WARMUP), "--no-spread", "--cpu-outers", "1",
+                                      "--forms", "fp64+mom,mixed+fused+r8"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_ours(bench.parse())
+    out = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(out) == 1
+    d = json.loads(out[0])
+
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks", "cpu_baseline"):
+        assert k in d, k
+    assert d["value"] == pytest.approx(EVENT_MS / STEPS / 1e3) and d["ms_per_step"] == pytest.approx(EVENT_MS / STEPS)
+    assert (d["n_gpus"], d["steps"], d["warmup"], d["unit"]) == (1, STEPS, WARMUP, "s")
+    assert d["higher_is_better"] is False and d["scaling"] == "weak" and d["vs_baseline"] is None
+    assert d["dtype"] == "f64" and d["config"]["workload"].startswith(f"poisson3d_7pt_{SIDE}")
+
+    n = SIDE ** 3
+    assert d["e2e"]["unit"] == "s" and d["e2e"]["value"] is not None
+    assert (d["e2e"]["h2d_bytes_per_step"], d["e2e"]["d2h_bytes_per_step"]) == (16 * n, 8 * n)
+    assert d["gpu_launches"] == STEPS * LAUNCHES
+
+    roof = d["roofline"]
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel"):
+        assert k in roof, k
+    assert roof["bound"] in ("alu", "hbm") and roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    # 8 step launches at 0.1 ms against one Gram at 0.3 and one update at 0.2: the step dominates
+    assert roof["kernel"] == "cheb_step" and roof["avg_launch_ms"] == pytest.approx(0.1)
+
+    cpu = d["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] > 0 and cpu["sample"]
+    assert cpu["all_cores"]["cores"] >= 1
+
+    forms = d["forms"]
+    assert set(forms) == {"fp64+mom", "mixed+fused+r8"}
+    assert forms["mixed+fused+r8"]["fp32_step"] == "tma" and forms["fp64+mom"]["fp32_step"] is None
+    assert forms["mixed+fused+r8"]["speedup_vs"] == "fp64+mom"
+    assert forms["fp64+mom"]["ms_per_outer"] == pytest.approx(EVENT_MS / STEPS / OUTERS)
+
+    # one output vector per form: every device solve of a form writes the same address, and the
+    # end-to-end leg runs the warm-up and the timed host solves of the headline form
+    ptrs = fake_gpu["device"]
+    per_form = WARMUP + STEPS + 2           # + the two host-loop solves that sample the kernels
+    assert len(ptrs) == 2 * per_form
+    assert len(set(ptrs[:per_form])) == 1 and len(set(ptrs[per_form:])) == 1
+    assert fake_gpu["host"] == WARMUP + STEPS
