@@ -130,3 +130,22 @@ def test_bench_line_carries_every_contract_key(fake_gpu, monkeypatch, capsys):
     assert len(ptrs) == 2 * per_form
     assert len(set(ptrs[:per_form])) == 1 and len(set(ptrs[per_form:])) == 1
     assert fake_gpu["host"] == WARMUP + STEPS
+
+
+def test_sweep_line_reports_every_s_and_form(fake_gpu, monkeypatch, capsys):
+    """--workload sweep: one row per s in {4, 8, 12, 16} and form (FP64 moments, mixed fused
+    refresh every 8), each from its own solve's record, in one JSON line."""
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "sweep", "--side", str(SIDE), "--sweep-outers", "2",
+                                      "--steps", "1", "--warmup", "1"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_sweep(bench.parse())
+    out = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(out) == 1
+    d = json.loads(out[0])
+    rows = d["sweep"]
+    assert [(r["s"], r["form"]) for r in rows] == [(s, f) for s in (4, 8, 12, 16) for f in ("fp64+mom", "mixed+fused+r8")]
+    for r in rows:
+        assert r["fp32_step"] == ("tma" if r["form"].startswith("mixed") else None)
+        assert r["ms_per_outer"] == pytest.approx(EVENT_MS / 1 / 1e3 / OUTERS * 1e3)
+        assert r["dominant"]["kernel"] == "cheb_step" and r["outer_iters"] == OUTERS
+    assert d["config"]["workload"] == f"poisson3d_7pt_{SIDE}^3_s_sweep"
