@@ -149,3 +149,29 @@ def test_sweep_line_reports_every_s_and_form(fake_gpu, monkeypatch, capsys):
         assert r["ms_per_outer"] == pytest.approx(EVENT_MS / 1 / 1e3 / OUTERS * 1e3)
         assert r["dominant"]["kernel"] == "cheb_step" and r["outer_iters"] == OUTERS
     assert d["config"]["workload"] == f"poisson3d_7pt_{SIDE}^3_s_sweep"
+
+
+@pytest.mark.parametrize("extra,workload", [
+    (["--workload", "poisson27"], "poisson3d_27pt_8^3"),
+    (["--workload", "poisson2d_64"], "poisson2d_5pt_64^2"),
+    (["--workload", "diffusion3d", "--no-cpu-baseline"], "diffusion3d_7pt_8^3_lognormal1"),
+    (["--csr"], "poisson3d_7pt_8^3_csr"),
+])
+def test_other_workload_lines(fake_gpu, monkeypatch, capsys, extra, workload):
+    """The other workloads' lines (27-point box stencil, 2D CSR, 3D diffusion, 3D Poisson as
+    CSR) carry the same keys; the CSR lines count the matrix bytes in their roofline."""
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--side", str(SIDE), "--steps", "1", "--warmup", "1", "--no-spread",
+                                      "--cpu-outers", "1", "--forms", "fp64+mom,mixed+mom"] + extra)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_ours(bench.parse())
+    out = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(out) == 1
+    d = json.loads(out[0])
+    assert d["config"]["workload"].startswith(workload), d["config"]
+    for k in ("metric", "value", "unit", "roofline", "e2e", "gpu_launches", "clocks", "cpu_baseline", "forms"):
+        assert k in d, k
+    assert set(d["forms"]) == {"fp64+mom", "mixed+mom"}
+    if "csr" in workload or "2d" in workload:
+        by = d["roofline"]["bytes_per_launch"]
+        n = 64 * 64 if "2d" in workload else SIDE ** 3
+        assert by > 24 * n   # the step reads the matrix: 12 nnz/n + 4 bytes per row on top of the vectors
