@@ -158,7 +158,9 @@ SSTEP_API sstep_status sstep_cg_create_csr(sstep_cg_t* handle, int64_t n, const 
                                  const int32_t* colind_d, const double* vals_d,
                                  const sstep_cg_opts* opts, void* stream);
 
-/* Matrix-free handle over a structured grid with homogeneous Dirichlet boundaries.
+/* Matrix-free handle over a structured grid with homogeneous Dirichlet boundaries: the
+ * synthetic Poisson problems of Section 8 (its 27-point stencil is sstep_cg_create_box_stencil)
+ * and a diffusion operator the paper does not discretise (the reading below).
  * dim = 2 (nz must be 1) or 3. kappa_d = NULL: the unscaled Poisson stencil, diagonal 2*dim
  * and -1 per in-grid neighbour (5- or 7-point). kappa_d = double[n] > 0: cell-centred
  * diffusion -div(kappa grad u); an interior face between cells a, b has weight
@@ -183,14 +185,22 @@ SSTEP_API sstep_status sstep_cg_create_stencil(sstep_cg_t* handle, int dim, int 
 SSTEP_API sstep_status sstep_cg_create_box_stencil(sstep_cg_t* handle, int dim, int nx, int ny, int nz,
                                                    const sstep_cg_opts* opts, void* stream);
 
-/* Solves A x = b from the initial guess in x_d (in: x_0, out: x). b_d, x_d: double[n].
- * info may be NULL. Synchronises the handle's stream (it reads the convergence state).
- * Returns SSTEP_OK when ||b - A x|| / ||b - A x_0|| < tol, SSTEP_ERR_NO_CONVERGENCE when
- * max_outer outers or max_refresh restarts did not get there (x holds the last iterate). */
+/* Solves A x = b by the s-step CG outer iteration of Section 2 (Chebyshev basis, Gram system,
+ * column scaling, nu FGS sweeps, update of x and r), stopped by the rule of Section 8 on the
+ * relative residual (the recursive one, with the true residual b - A x checked at exit).
+ * b_d, x_d: device double[n], 16-byte aligned, caller-owned (in: x_0, out: x); info (host)
+ * may be NULL. Synchronises the handle's stream (it reads the convergence state). Returns
+ * SSTEP_OK when ||b - A x|| / ||b - A x_0|| < tol, SSTEP_ERR_NO_CONVERGENCE when max_outer
+ * outers or max_refresh restarts did not get there (x holds the last iterate),
+ * SSTEP_ERR_NUMERICAL when the Gram system breaks down (every column dropped, a non-finite
+ * entry), SSTEP_ERR_TIMEOUT when a bounded device-side wait expired, SSTEP_ERR_INVALID_ARG for
+ * a null or misaligned pointer. */
 SSTEP_API sstep_status sstep_cg_solve(sstep_cg_t handle, const double* b_d, double* x_d, sstep_cg_info* info);
 
-/* Same solve with HOST arrays b_h, x_h (double[n], pinned or pageable): copies b and x_0 to
- * the handle's device buffers, solves, copies x back. Synchronises. */
+/* The solve of sstep_cg_solve (Section 2) with HOST arrays b_h, x_h (double[n], pinned or
+ * pageable, caller-owned): copies b and x_0 to device buffers the handle owns (allocated on
+ * the first call), solves, copies x back; info.ms includes the copies. Same statuses; x_h is
+ * written unless the solve failed with a CUDA, memory or timeout error. Synchronises. */
 SSTEP_API sstep_status sstep_cg_solve_host(sstep_cg_t handle, const double* b_h, double* x_h, sstep_cg_info* info);
 
 /* Differentiable solve (adjoint): for a diffusion stencil handle (created with kappa_d) and a
@@ -214,8 +224,9 @@ SSTEP_API sstep_status sstep_cg_grad_kappa(sstep_cg_t handle, const double* x_d,
  * no history. Synchronises the handle's stream. */
 SSTEP_API sstep_status sstep_cg_history(sstep_cg_t handle, double* out_h, int capacity, int* count);
 
-/* Changes the stopping tolerance and the outer-iteration limit of an existing handle (for
- * example a looser tolerance for an adjoint solve that reuses the forward handle). */
+/* Changes the tolerance of Section 8's stopping rule and the outer-iteration limit of an
+ * existing handle (for example a looser tolerance for an adjoint solve that reuses the
+ * forward handle). SSTEP_ERR_INVALID_ARG unless tol > 0 is finite and max_outer >= 0. */
 SSTEP_API sstep_status sstep_cg_set_tolerance(sstep_cg_t handle, double tol, int max_outer);
 
 /* Releases the handle and everything it owns (synchronises its stream). NULL is a no-op. */
@@ -229,7 +240,8 @@ SSTEP_API const char* sstep_cg_last_error(sstep_cg_t handle);
 
 /* --- operator and pipeline pieces (the solve is composed of these kernels) ----------- */
 
-/* y_d = A x_d with the handle's operator (double[n] each). */
+/* y_d = A x_d with the handle's operator, the A of Section 2's system (device double[n]
+ * each, caller-owned). Asynchronous on the handle's stream. */
 SSTEP_API sstep_status sstep_cg_apply(sstep_cg_t handle, const double* x_d, double* y_d);
 
 /* Chebyshev basis of Section 2 (Definition): column j of P_d (leading dimension ldp >= n,
@@ -243,14 +255,17 @@ SSTEP_API sstep_status sstep_cg_basis(sstep_cg_t handle, const double* r_d, doub
  * Run after sstep_cg_load_basis. Synchronises. */
 SSTEP_API sstep_status sstep_cg_gram_solve(sstep_cg_t handle, double* out_h);
 
-/* Copies a caller basis P_d (n x (s+1), leading dimension ldp; column 0 = r) into the handle's
- * basis workspace, for sstep_cg_gram_solve. */
+/* Copies a caller basis P_d (the P_+ = [p_0 .. p_s] of Section 2: device doubles, n x (s+1),
+ * column-major, leading dimension ldp >= n; column 0 = r) into the handle's basis workspace,
+ * for sstep_cg_gram_solve. SSTEP_ERR_INVALID_ARG for a null pointer or ldp < n. */
 SSTEP_API sstep_status sstep_cg_load_basis(sstep_cg_t handle, const double* P_d, int64_t ldp);
 
-/* Spectral bounds the handle uses (after create): lambda_min, lambda_max (host doubles). */
+/* Spectral bounds the handle uses (given, or Section 8's Gershgorin / Lanczos estimates,
+ * computed at create): lambda_min, lambda_max (host doubles). */
 SSTEP_API sstep_status sstep_cg_get_bounds(sstep_cg_t handle, double* lambda_min, double* lambda_max);
 
-/* Writes the handle's current residual r (column 0 of the basis workspace) to r_d. */
+/* Writes the handle's current residual r_k of Section 2 (column 0 of the basis workspace) to
+ * r_d (device double[n]). Asynchronous on the handle's stream. */
 SSTEP_API sstep_status sstep_cg_get_residual(sstep_cg_t handle, double* r_d);
 
 /* Lanczos tridiagonal of Section 8's estimate: k steps on D^-1/2 A D^-1/2 from the seeded
@@ -258,7 +273,8 @@ SSTEP_API sstep_status sstep_cg_get_residual(sstep_cg_t handle, double* r_d);
 SSTEP_API sstep_status sstep_cg_lanczos(sstep_cg_t handle, int k, uint64_t seed, double* alpha_h, double* beta_h,
                               int* steps_done);
 
-/* The two conversions of the mixed form, exposed for testing: out_d[i] = float(in_d[i] * 2^k)
+/* The two conversions of the mixed form (FP32 basis, FP64 Gram and x; the paper has no mixed
+ * form), exposed for testing: out_d[i] = float(in_d[i] * 2^k)
  * rounded to nearest even, computed from the IEEE-754 fields with integer instructions, and
  * back_d[i] = double(out_d[i]), exact. Device arrays of n elements; asynchronous on stream. */
 SSTEP_API sstep_status sstep_convert_check(const double* in_d, int k, float* out_d, double* back_d, int64_t n,
@@ -305,25 +321,32 @@ typedef struct sstep_cg_batch_s* sstep_cg_batch_t;
 SSTEP_API sstep_status sstep_cg_batch_create(sstep_cg_batch_t* batch, int count, const int* grids_h,
                                              const double* const* kappa_d, const sstep_cg_opts* opts, void* stream);
 
-/* offsets_h (host int64[count], may be NULL): start of each system in the concatenated
+/* Layout of the batched form (not in the paper; the per-system solve is Section 2's):
+ * offsets_h (host int64[count], may be NULL): start of each system in the concatenated
  * vectors; total: their length; lambda_h (host double[2*count], may be NULL): the bounds. */
 SSTEP_API sstep_status sstep_cg_batch_layout(sstep_cg_batch_t batch, int64_t* offsets_h, int64_t* total,
                                              double* lambda_h);
 
-/* Solves all systems from x_0 = x_d (concatenated, device). infos_h (host, count entries, may
- * be NULL) receives each system's result; summary (may be NULL) the largest outer count, the
- * worst true relative residual and the device time. Returns SSTEP_OK when every system
- * reached tol, else the first failing status. Synchronises. */
+/* Solves all systems by Section 2's outer iteration, each with its own Gram system and
+ * Section 8's stopping rule, from x_0 = x_d (concatenated, device, caller-owned; b_d alike).
+ * infos_h (host, count entries, may be NULL) receives each system's result; summary (may be
+ * NULL) the largest outer count, the worst true relative residual and the device time.
+ * Returns SSTEP_OK when every system reached tol, else the first failing status. Synchronises. */
 SSTEP_API sstep_status sstep_cg_batch_solve(sstep_cg_batch_t batch, const double* b_d, double* x_d,
                                             sstep_cg_info* infos_h, sstep_cg_info* summary);
 
+/* Releases the batch and everything it owns (synchronises its stream). NULL is a no-op. */
 SSTEP_API sstep_status sstep_cg_batch_destroy(sstep_cg_batch_t batch);
+
+/* Text of the last error recorded on the batch; with batch = NULL, the reason of the last
+ * failed create (as sstep_cg_last_error(NULL); "" if none). */
 SSTEP_API const char* sstep_cg_batch_last_error(sstep_cg_batch_t batch);
 
 /* --- allocation-free variant ---------------------------------------------------------- */
 
-/* The Gram reduction, column scaling and FGS (or Cholesky) solve of one outer iteration -
- * the same kernel and results as sstep_cg_gram_solve - for callers that cannot allocate
+/* The Gram reduction, column scaling and FGS (or Cholesky) solve of one outer iteration
+ * (Section 2's Gram system and scaling, Section 3's sweeps) - the same kernel and results as
+ * sstep_cg_gram_solve - for callers that cannot allocate
  * device memory, e.g. because a caching allocator already owns the device's memory or
  * because cudaMalloc/cudaFree would synchronise the device inside a latency-bound loop. It
  * needs no handle and allocates nothing: its scratch (per-block partial sums and a control
