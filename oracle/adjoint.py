@@ -23,12 +23,15 @@ import numpy as np
 
 
 def _shape(dims):
+    """The (nz, ny, nx) array shape of a grid and its dimension (no arithmetic of the method)."""
     nx, ny, nz = (tuple(dims) + (1, 1))[:3]
     return (nz, ny, nx), (3 if len(dims) == 3 else 2)
 
 
 def grad_kappa(dims, kappa, x, lam):
-    """dL/dkappa from the forward solution x and the adjoint solution lambda."""
+    """dL/dkappa from the forward solution x and the adjoint solution lambda. The paper has
+    no adjoint: this differentiates the solve of Section 2 through the diffusion operator
+    (the module docstring gives the formula)."""
     shape, d = _shape(dims)
     K = np.asarray(kappa, np.float64).reshape(shape)
     X = np.asarray(x, np.float64).reshape(shape)
@@ -56,7 +59,8 @@ def grad_kappa(dims, kappa, x, lam):
 
 
 def loss_and_grad(dims, kappa, b, x_target, solve_fn):
-    """L, dL/dkappa, dL/db with `solve_fn(rhs) -> A(kappa)^-1 rhs` (forward and adjoint)."""
+    """L, dL/dkappa, dL/db with `solve_fn(rhs) -> A(kappa)^-1 rhs` (forward and adjoint
+    solves of Section 2's method; the paper has no adjoint)."""
     x = solve_fn(b)
     g = 2.0 * (x - x_target)
     lam = solve_fn(g)

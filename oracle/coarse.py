@@ -27,7 +27,8 @@ from .sstep_cg import Operator, fgs
 def box_aggregates(dims, block):
     """Aggregate id of every fine point for aggregates that are block[0] x block[1] (x
     block[2]) boxes of the grid (the last box along an axis may be smaller), ids ordered
-    x fastest over the coarse grid; returns (agg, n_c, coarse dims)."""
+    x fastest over the coarse grid; returns (agg, n_c, coarse dims). Section 6 takes P from
+    an AMG hierarchy; box aggregation stands in for it (a reading)."""
     nx, ny, nz = (tuple(dims) + (1, 1))[:3]
     bx, by, bz = (tuple(block) + (1, 1))[:3]
     cx, cy, cz = -(-nx // bx), -(-ny // by), -(-nz // bz)
@@ -38,12 +39,14 @@ def box_aggregates(dims, block):
 
 
 def prolongation(agg, n_c):
+    """The aggregation prolongation P (n_f x n_c, column i the indicator of aggregate i) that
+    stands in for the P of Section 6."""
     n_f = len(agg)
     return sp.csr_matrix((np.ones(n_f), (np.arange(n_f), agg)), shape=(n_f, n_c))
 
 
 def coarse_operator(op: Operator, agg, n_c):
-    """A_c = P^T A_f P (dense)."""
+    """A_c = P^T A_f P (dense), the coarse operator of Section 6."""
     P = prolongation(agg, n_c)
     return (P.T @ (op.A @ P)).toarray()
 
@@ -54,7 +57,8 @@ def coarse_fgs(Ac, g, nu: int, y0=None):
 
 
 def coarse_fgs_streaming(op: Operator, agg, n_c: int, g, nu: int, y0=None):
-    """The same sweeps with A_c never formed: rows of A_c y from the fine level."""
+    """The same sweeps with A_c never formed (Section 6's streaming form): rows of A_c y
+    from the fine level."""
     agg = np.asarray(agg)
     g = np.asarray(g, np.float64)
     y = np.zeros(n_c) if y0 is None else np.array(y0, dtype=np.float64)

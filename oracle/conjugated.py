@@ -44,7 +44,8 @@ def scaled_solve(W, rhs, nu: int, solver: str = "fgs"):
 def solve_conjugated(op: Operator, b, x0=None, *, s: int, nu: int, lam_min: float, lam_max: float,
                      tol: float = 1e-8, max_outer: int = 100000, gram_solver: str = "fgs",
                      max_refresh: int = 3, history: int = 0) -> SolveResult:
-    """Block-conjugated s-step CG with the Chebyshev basis (steps 1-5 of the module docstring)."""
+    """Block-conjugated s-step CG (Chronopoulos and Gear, the method Section 1 cites) with
+    the Chebyshev basis of Section 2 (steps 1-5 of the module docstring)."""
     b = np.asarray(b, np.float64)
     x = np.zeros(op.n) if x0 is None else np.array(x0, dtype=np.float64)
     r = b - op.matvec(x)

@@ -18,7 +18,8 @@ from .sstep_cg import Operator
 
 
 def lanczos(op: Operator, v0, k: int = 10):
-    """k steps of Lanczos on B = D^-1/2 A D^-1/2: returns (alpha[0:m], beta[0:m-1])."""
+    """k steps of Lanczos on B = D^-1/2 A D^-1/2 (Section 8's eigenvalue estimate): returns
+    (alpha[0:m], beta[0:m-1])."""
     dh = np.sqrt(op.minv)                  # D^-1/2
     q = np.asarray(v0, np.float64) / np.linalg.norm(v0)
     q_prev = np.zeros_like(q)
@@ -39,7 +40,8 @@ def lanczos(op: Operator, v0, k: int = 10):
 
 
 def sturm_count(alpha, beta, x: float) -> int:
-    """Number of eigenvalues of the symmetric tridiagonal (alpha, beta) below x."""
+    """Number of eigenvalues of the symmetric tridiagonal (alpha, beta) below x (the Sturm
+    count behind the Ritz values of Section 8's Lanczos estimate)."""
     count = 0
     q = 1.0
     for i in range(len(alpha)):
@@ -53,7 +55,8 @@ def sturm_count(alpha, beta, x: float) -> int:
 
 
 def tridiag_eigvals(alpha, beta):
-    """All eigenvalues (ascending) of a symmetric tridiagonal matrix by bisection."""
+    """All eigenvalues (ascending) of a symmetric tridiagonal matrix by bisection: the Ritz
+    values of Section 8's Lanczos estimate."""
     m = len(alpha)
     if m == 0:
         return np.array([])
@@ -77,13 +80,14 @@ def tridiag_eigvals(alpha, beta):
 
 
 def gershgorin_upper(op: Operator) -> float:
-    """max_i sum_j |(M^-1 A)_ij|: Gershgorin upper bound on the spectrum of M^-1 A."""
+    """max_i sum_j |(M^-1 A)_ij|: Gershgorin upper bound on the spectrum of M^-1 A (the
+    upper end of the workloads' "Gershgorin/10-step Lanczos" bounds, a reading of Section 8)."""
     absrow = np.asarray(abs(op.A).sum(axis=1)).ravel()
     return float(np.max(np.abs(op.minv) * absrow))
 
 
 def bounds(op: Operator, mode: str, v0, k: int = 10):
-    """(lam_min, lam_max) under the two readings above."""
+    """(lam_min, lam_max) of Section 8 under the two readings above."""
     a, b = lanczos(op, v0, k)
     ev = tridiag_eigvals(a, b)
     if mode == "lanczos10":

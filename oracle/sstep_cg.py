@@ -120,7 +120,8 @@ def fgs(G, rhs, nu: int, alpha0=None):
 
 
 def fgs_iterates(G, rhs, nu: int, alpha0=None):
-    """All sweep iterates a^(0) .. a^(nu) of `fgs`."""
+    """All sweep iterates a^(0) .. a^(nu) of `fgs` (Section 2's sweep; Section 3 states its
+    residual structure in terms of them)."""
     s = G.shape[0]
     a = np.zeros(s) if alpha0 is None else np.array(alpha0, dtype=np.float64)
     out = [a.copy()]
@@ -139,7 +140,8 @@ def fgs_iterates(G, rhs, nu: int, alpha0=None):
 
 
 def cholesky(G):
-    """Plain Cholesky G = R^T R (R upper triangular); raises on a non-positive pivot."""
+    """Plain Cholesky G = R^T R (R upper triangular), the direct Gram factorisation that
+    Sections 1 and 8 compare FGS against; raises on a non-positive pivot."""
     s = G.shape[0]
     R = np.zeros_like(G)
     for j in range(s):
@@ -153,7 +155,8 @@ def cholesky(G):
 
 
 def cholesky_solve(G, rhs):
-    """Direct Gram solve by Cholesky and two triangular solves (the O(s^3) baseline)."""
+    """Direct Gram solve by Cholesky and two triangular solves (the O(s^3) baseline of
+    Sections 1 and 8)."""
     R = cholesky(G)
     s = G.shape[0]
     y = np.zeros(s)
@@ -166,6 +169,8 @@ def cholesky_solve(G, rhs):
 
 
 def _gram_solve_scaled(Gt, ct, nu, solver):
+    """a from the scaled Gram system G~ a = c~ of Section 2: nu FGS sweeps, or Cholesky on the
+    kept (non-dropped) columns for the direct comparison of Sections 1 and 8."""
     if solver == "fgs":
         return fgs(Gt, ct, nu)
     if solver == "cholesky":
