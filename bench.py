@@ -192,11 +192,12 @@ def measured_traffic(workload, form, logical):
     return None
 
 
-# FP64 issue rate measured on GB300 (profiles/fp64_issue_rate_gb300.md): FMAs at 627.9 G
-# lane-operations/s (2 per SM per clock at 2070 MHz, 152 SMs); adds and multiplies issue at
-# only 528 G, which is why the FP64 stencils write their additions as FMAs.
+# FP64 issue rate measured on GB300 by paper_2512_09642_gb300/microbench/fp64_rate.cu: FMAs at
+# 627.9 G lane-operations/s (2 per SM per clock at 2070 MHz, 152 SMs); adds and multiplies
+# issue at only 528 G, which is why the FP64 stencils write their additions as FMAs.
 FP64_OPS_PEAK = 0.6279e12
-FP64_PEAK_KIND = "measured: FP64 FMA issue rate, 627.9 G lane-ops/s at 2070 MHz (profiles/fp64_issue_rate_gb300.md)"
+FP64_PEAK_KIND = ("measured: FP64 FMA issue rate, 627.9 G lane-ops/s at 2070 MHz "
+                  "(paper_2512_09642_gb300/microbench/fp64_rate.cu)")
 
 
 def form_gram(form):
