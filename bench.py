@@ -664,11 +664,11 @@ def run_ours(args):
             forms[prec]["rel_diff_vs_fp64_x"] = float(torch.linalg.norm(res[prec]["x"] - x64) / torch.linalg.norm(x64))
     head = args.forms.split(",")[0]
     h = forms[head]
-    if h["roofline"]:
-        tr = measured_traffic(wname, head, h["roofline"].get("kernel"))
+    for prec, f in forms.items():   # ncu DRAM bytes per launch where a capture of this kernel exists
+        tr = measured_traffic(wname, prec, f["roofline"].get("kernel")) if f["roofline"] else None
         if tr:
-            h["roofline"]["traffic"] = tr["bytes"]
-            h["roofline"]["traffic_source"] = f"ncu capture of {tr['kernel']}, profiles/{tr['profile']}"
+            f["roofline"]["traffic"] = tr["bytes"]
+            f["roofline"]["traffic_source"] = f"ncu capture of {tr['kernel']}, profiles/{tr['profile']}"
 
     spread = None
     if args.workload == "poisson3d" and csr is None and not args.no_spread:
