@@ -170,7 +170,8 @@ def kernel_source_sha(path, kernel):
     """sha256 of a kernel's __global__ definition (up to its closing brace at column 0)."""
     import hashlib
     src = open(os.path.join(ROOT, path)).read()
-    m = re.search(r"__global__ void __launch_bounds__\([^)]*\) " + re.escape(kernel) + r"\(", src)
+    # the launch bounds may hold one level of parentheses (a constexpr call)
+    m = re.search(r"__global__ void __launch_bounds__\((?:[^()]|\([^()]*\))*\) " + re.escape(kernel) + r"\(", src)
     if not m:
         return None
     end = src.find("\n}\n", m.start())

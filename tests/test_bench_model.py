@@ -55,6 +55,8 @@ def test_stored_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
         tok = line.split()
         if line.startswith("#") or len(tok) < 7:
             continue
+        # every named kernel's definition is found (launch bounds may hold a constexpr call)
+        assert bench.kernel_source_sha(tok[4], tok[3]) is not None, tok[3]
         current = bench.kernel_source_sha(tok[4], tok[3]) == tok[6]
         monkeypatch.setattr(bench, "TRAFFIC", os.path.join(ROOT, "profiles", "traffic.txt"))
         assert (bench.measured_traffic(tok[0], tok[1], tok[2]) is not None) == current
