@@ -259,3 +259,26 @@ def test_every_declaration_is_documented_and_cited():
             comment = before[before.rfind("/*"):]
             if m.group(1) not in plumbing:
                 assert "Section" in comment or "paper" in comment, f"{m.group(1)} cites no passage"
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """With no built library next to it, importing the binding (and so SStepCG) raises: there is
+    no CPU fallback on the product path. Checked on a copy of the package's Python files."""
+    import shutil
+    import sys
+    pkg = os.path.join(ROOT, "paper_2512_09642_gb300")
+    dst = tmp_path / "paper_2512_09642_gb300"
+    dst.mkdir()
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(pkg, f), dst / f)
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "try:\n"
+            "    from paper_2512_09642_gb300 import SStepCG\n"
+            "except ImportError as e:\n"
+            "    print('raised', e)\n"
+            "else:\n"
+            "    print('imported')\n") % str(tmp_path)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path))
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.startswith("raised") and "libsstep_cg.so is missing" in r.stdout, r.stdout + r.stderr
