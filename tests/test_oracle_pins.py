@@ -710,3 +710,29 @@ def test_every_oracle_function_cites_its_passage():
             if isinstance(node, ast.FunctionDef) and (not node.name.startswith("_") or node.name == "_gram_solve_scaled"):
                 doc = ast.get_docstring(node) or ""
                 assert any(w in doc for w in words), f"{os.path.basename(f)}:{node.name}"
+
+
+def test_oracle_and_library_share_no_code():
+    """The CUDA library's Python side never imports the oracle, the oracle never imports the
+    library, and the seeded input generators (`workloads`) import neither."""
+    import ast
+    import glob
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+    def imported(path):
+        mods = set()
+        for node in ast.walk(ast.parse(open(path).read())):
+            if isinstance(node, ast.Import):
+                mods |= {a.name.split(".")[0] for a in node.names}
+            elif isinstance(node, ast.ImportFrom) and node.level == 0 and node.module:
+                mods.add(node.module.split(".")[0])
+        return mods
+
+    for f in glob.glob(os.path.join(root, "paper_2512_09642_gb300", "*.py")):
+        assert "oracle" not in imported(f), f
+    for f in glob.glob(os.path.join(root, "oracle", "*.py")):
+        assert "paper_2512_09642_gb300" not in imported(f), f
+    for f in glob.glob(os.path.join(root, "workloads", "*.py")):
+        assert not imported(f) & {"oracle", "paper_2512_09642_gb300"}, f
+    for f in glob.glob(os.path.join(root, "paper_2512_09642_gb300", "csrc", "*")):
+        assert "oracle" not in open(f).read(), f
