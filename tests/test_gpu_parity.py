@@ -232,6 +232,29 @@ def test_edge_cases():
         assert _rel(x.cpu().numpy(), ref.history[-1].x) <= 1e-9, dims
 
 
+def test_resume_from_a_saved_iterate():
+    """Checkpoint and resume: the restarted iteration's state is x, so a solve started from a
+    saved iterate (the oracle's x_3, nx even: the register-blocked steps) continues as the
+    oracle continues from it: its two resumed iterates agree to 1e-10 for both Gram forms, and
+    the resumed solve reaches 1e-8 relative to its own starting residual."""
+    p = W.make("p3", (20, 13, 11), config=12)
+    op = O.Operator(*p.csr())
+    lam = OS.bounds(op, "gersh_lanczos10", W.lanczos_start(p.n))
+    kw = dict(s=8, nu=25, lam_min=lam[0], lam_max=lam[1], tol=1e-30)
+    x3 = O.solve(op, p.b, max_outer=3, **kw).x
+    ref = O.solve(op, p.b, x3, max_outer=2, history=2, **kw)
+    for form in ("direct", "moments"):
+        sv = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-30, max_outer=2, gram_form=form, check_every=1)
+        x, info = sv.solve(_dev(p.b), _dev(x3))
+        sv.close()
+        assert info["outer_iters"] == 2, info
+        assert _rel(x.cpu().numpy(), ref.history[-1].x) <= 1e-10, form
+    sv = _solver(p, "stencil", bounds=lam, s=8, nu=25, tol=1e-8)
+    x, info = sv.solve(_dev(p.b), _dev(x3))
+    sv.close()
+    assert info["status"] == "SSTEP_OK" and info["rel_res_true"] <= 1e-8, info
+
+
 def test_host_buffer_solve_matches_device_solve():
     from paper_2512_09642_gb300 import abi
     p = W.poisson2d_64()

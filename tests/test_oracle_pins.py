@@ -461,6 +461,21 @@ def test_minv_r_start_equals_r_start_for_constant_preconditioner(dims):
     assert np.linalg.norm(a.history[0].x - b.history[0].x) > 1e-3 * np.linalg.norm(a.history[0].x)
 
 
+def test_resuming_from_an_iterate_continues_the_iteration():
+    """Section 2's outer iteration is restarted: its state is x alone (r = b - A x). Stopping
+    after 3 outer iterations and solving again from x_3 gives the uninterrupted run's x_5, up
+    to the rounding of the recomputed residual."""
+    p = W.make("p3", (20, 13, 11), config=12)
+    op = O.Operator(*p.csr())
+    kw = dict(s=8, nu=25, lam_min=0.04, lam_max=2.0, tol=1e-30)
+    run = O.solve(op, p.b, max_outer=5, history=5, **kw)
+    x3 = O.solve(op, p.b, max_outer=3, **kw).x
+    assert np.linalg.norm(x3 - run.history[2].x) == 0.0
+    resumed = O.solve(op, p.b, x3, max_outer=2, history=2, **kw)
+    assert resumed.outer_iters == 2
+    assert np.linalg.norm(resumed.history[-1].x - run.history[-1].x) <= 1e-13 * np.linalg.norm(run.history[-1].x)
+
+
 def test_tiny_system_one_outer_with_cholesky_is_exact():
     n = 5
     M = rng.uniform(31, n * n).reshape(n, n)
