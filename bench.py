@@ -420,7 +420,8 @@ def poisson3d_config(side, s, nu, box=False):
     return {"workload": f"poisson3d_27pt_{side}^3" if box else f"poisson3d_7pt_{side}^3", "n": side ** 3,
             "operator": "3D 27-point Poisson" if box else "3D 7-point Poisson", "s": s, "nu": nu,
             "precond": "jacobi", "bounds": "lanczos10 (both ends, 10% margins)" if box else "gershgorin + lanczos10",
-            "tol": 1e-8, "l2": "inputs larger than L2", "x0": "zero", "b": "A x*, x* ~ U(-1,1)"}
+            "tol": 1e-8, "l2": "inputs larger than L2" if side ** 3 * 8 * (s + 1) > 129e6 else "inputs fit in L2",
+            "x0": "zero", "b": "A x*, x* ~ U(-1,1)"}
 
 
 # ---- arms ------------------------------------------------------------------------------------
