@@ -175,3 +175,34 @@ def test_other_workload_lines(fake_gpu, monkeypatch, capsys, extra, workload):
         by = d["roofline"]["bytes_per_launch"]
         n = 64 * 64 if "2d" in workload else SIDE ** 3
         assert by > 24 * n   # the step reads the matrix: 12 nnz/n + 4 bytes per row on top of the vectors
+
+
+def test_a_failing_secondary_form_is_reported_not_fatal(fake_gpu, monkeypatch, capsys):
+    """A secondary form whose solve raises is recorded as an error in `forms`; the headline line
+    is still printed (a failing headline form ends the run)."""
+    from paper_2512_09642_gb300 import abi
+    good = abi.sstep_cg_solve
+
+    def solve(h, b, x, allow=(5,)):
+        info = good(h, b, x, allow)
+        if info.mixed:
+            raise abi.SStepError(4, "out of memory (stand-in)")
+        return info
+
+    monkeypatch.setattr(abi, "sstep_cg_solve", solve)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--side", str(SIDE), "--steps", "1", "--warmup", "1", "--no-spread",
+                                      "--no-cpu-baseline", "--forms", "fp64+mom,mixed+fused+r8"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_ours(bench.parse())
+    out = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(out) == 1
+    d = json.loads(out[0])
+    assert d["form"] == "fp64+mom" and d["value"] > 0
+    assert "out of memory" in d["forms"]["mixed+fused+r8"]["error"]
+    assert "speedup_vs" not in d["forms"]["fp64+mom"]
+
+    # the headline form failing is fatal
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--side", str(SIDE), "--steps", "1", "--warmup", "1", "--no-spread",
+                                      "--no-cpu-baseline", "--forms", "mixed+fused+r8,fp64+mom"])
+    with pytest.raises(abi.SStepError):
+        bench.run_ours(bench.parse())
