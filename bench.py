@@ -590,6 +590,32 @@ def kernel_report(args, n, infos, precision, dim=3, diffusion=False, box=False, 
     return roof, table
 
 
+def xstar_spread(args, p, b, side, head):
+    """The headline form on the five seeded x* (the first is the workload's): the outer count
+    to 1e-8 of this restarted iteration moves with rounding, the time per outer iteration does
+    not."""
+    import torch
+    from paper_2512_09642_gb300 import SStepCG, abi
+    from workloads import problems as W
+    s, nu, n = args.s, args.nu, p.n
+    parts = head.split("+")
+    sv = SStepCG(grid=p.dims, s=s, nu=nu, tol=1e-8, check_every=8, precision=parts[0], gram_form=form_gram(head),
+                 block_conjugate=1 if "conj" in parts else 0, use_graph=0 if args.host_loop else 1,
+                 refresh_period=form_refresh(head) if parts[0] == "mixed" else 1)
+    runs = []
+    for sd in SPREAD_SEEDS:
+        bq = b if sd == SPREAD_SEEDS[0] else torch.as_tensor(W.poisson3d(side, xstar_seed=sd).b).cuda()
+        xq = torch.zeros(n, dtype=torch.float64, device="cuda")
+        inf = abi.sstep_cg_solve(sv.h, bq, xq).as_dict()
+        runs.append({"xstar_seed": sd, "outer_iters": inf["outer_iters"], "time_s": inf["ms"] / 1e3,
+                     "ms_per_outer": inf["ms"] / max(inf["outer_iters"], 1), "rel_res_true": inf["rel_res_true"]})
+    sv.close()
+    cnt = sorted(r["outer_iters"] for r in runs)
+    tms = sorted(r["time_s"] for r in runs)
+    return {"form": head, "outer_min": cnt[0], "outer_median": cnt[2], "outer_max": cnt[-1],
+            "time_median_s": tms[2], "runs": runs}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -682,26 +708,10 @@ def run_ours(args):
 
     spread = None
     if args.workload == "poisson3d" and csr is None and not args.no_spread:
-        # the headline form on the five seeded x* (the first is the workload's): the outer
-        # count to 1e-8 of this restarted iteration moves with rounding, the time per outer
-        # iteration does not
-        from paper_2512_09642_gb300 import SStepCG, abi
-        parts = head.split("+")
-        sv = SStepCG(grid=p.dims, s=s, nu=nu, tol=1e-8, check_every=8, precision=parts[0], gram_form=form_gram(head),
-                     block_conjugate=1 if "conj" in parts else 0, use_graph=0 if args.host_loop else 1,
-                     refresh_period=form_refresh(head) if parts[0] == "mixed" else 1)
-        runs = []
-        for sd in SPREAD_SEEDS:
-            bq = b if sd == SPREAD_SEEDS[0] else torch.as_tensor(W.poisson3d(side, xstar_seed=sd).b).cuda()
-            xq = torch.zeros(n, dtype=torch.float64, device="cuda")
-            inf = abi.sstep_cg_solve(sv.h, bq, xq).as_dict()
-            runs.append({"xstar_seed": sd, "outer_iters": inf["outer_iters"], "time_s": inf["ms"] / 1e3,
-                         "ms_per_outer": inf["ms"] / max(inf["outer_iters"], 1), "rel_res_true": inf["rel_res_true"]})
-        sv.close()
-        cnt = sorted(r["outer_iters"] for r in runs)
-        tms = sorted(r["time_s"] for r in runs)
-        spread = {"form": head, "outer_min": cnt[0], "outer_median": cnt[2], "outer_max": cnt[-1],
-                  "time_median_s": tms[2], "runs": runs}
+        try:
+            spread = xstar_spread(args, p, b, side, head)
+        except Exception as ex:   # the spread is context: it must not hide the headline line
+            spread = {"form": head, "error": f"{type(ex).__name__}: {ex}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("poisson3d", "poisson27"):

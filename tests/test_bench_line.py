@@ -206,3 +206,24 @@ def test_a_failing_secondary_form_is_reported_not_fatal(fake_gpu, monkeypatch, c
                                       "--no-cpu-baseline", "--forms", "mixed+fused+r8,fp64+mom"])
     with pytest.raises(abi.SStepError):
         bench.run_ours(bench.parse())
+
+
+def test_xstar_spread_and_its_failure(fake_gpu, monkeypatch, capsys):
+    """The headline line's `xstar_spread` (five seeded x*), and an error entry in its place when
+    it fails."""
+    argv = ["bench.py", "--side", str(SIDE), "--steps", "1", "--warmup", "1", "--no-cpu-baseline", "--forms", "fp64+mom"]
+    monkeypatch.setattr(sys, "argv", argv)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_ours(bench.parse())
+    d = json.loads([ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")][0])
+    sp = d["xstar_spread"]
+    assert [r["xstar_seed"] for r in sp["runs"]] == list(bench.SPREAD_SEEDS)
+    assert sp["outer_min"] <= sp["outer_median"] <= sp["outer_max"] and sp["form"] == "fp64+mom"
+
+    def broken(*a, **k):
+        raise RuntimeError("stand-in failure")
+
+    monkeypatch.setattr(bench, "xstar_spread", broken)
+    bench.run_ours(bench.parse())
+    d = json.loads([ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")][0])
+    assert d["xstar_spread"] == {"form": "fp64+mom", "error": "RuntimeError: stand-in failure"}
