@@ -227,3 +227,26 @@ def test_xstar_spread_and_its_failure(fake_gpu, monkeypatch, capsys):
     bench.run_ours(bench.parse())
     d = json.loads([ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")][0])
     assert d["xstar_spread"] == {"form": "fp64+mom", "error": "RuntimeError: stand-in failure"}
+
+
+def test_coarse_line(fake_gpu, monkeypatch, capsys):
+    """--workload coarse: both modes timed (streaming the headline), their memory footprints
+    (n_c^2 doubles formed, n_f + n_c streaming) and the line's keys."""
+    from paper_2512_09642_gb300 import abi
+    calls = []
+
+    def coarse(h, block, g, y, nu, mode):
+        calls.append((tuple(block), nu, mode))
+        y.fill_(1.0)
+
+    monkeypatch.setattr(abi, "sstep_coarse_fgs", coarse)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "coarse", "--steps", "2", "--warmup", "1"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_coarse(bench.parse())
+    d = json.loads([ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")][0])
+    nc, nf = 16 ** 3, 128 ** 3
+    assert d["config"]["n_coarse"] == nc and d["config"]["n_fine"] == nf
+    assert d["modes"]["formed"]["extra_device_bytes"] == nc * nc * 8
+    assert d["modes"]["streaming"]["extra_device_bytes"] == (nf + nc) * 8
+    assert d["value"] == pytest.approx(EVENT_MS / 2 / 1e3) == d["modes"]["streaming"]["time_s"]
+    assert calls == [((8, 8, 8), 20, "streaming")] * 3 + [((8, 8, 8), 20, "formed")] * 3
