@@ -250,3 +250,41 @@ def test_coarse_line(fake_gpu, monkeypatch, capsys):
     assert d["modes"]["streaming"]["extra_device_bytes"] == (nf + nc) * 8
     assert d["value"] == pytest.approx(EVENT_MS / 2 / 1e3) == d["modes"]["streaming"]["time_s"]
     assert calls == [((8, 8, 8), 20, "streaming")] * 3 + [((8, 8, 8), 20, "formed")] * 3
+
+
+def test_adjoint_line(fake_gpu, monkeypatch, capsys):
+    """--workload adjoint: forward + backward timed, the directional gradient check against the
+    assembled dL/dkappa, and the line's keys (solves and the assembly replaced by stand-ins:
+    x = b, lambda = the adjoint right-hand side, dL/dkappa = lambda)."""
+    import paper_2512_09642_gb300 as pkg
+    from paper_2512_09642_gb300 import abi, autograd
+
+    class Solver:
+        def __init__(self, **kw):
+            self.h = object()
+            self.opts = abi.sstep_cg_default_opts()
+
+        def solve(self, b, x0=None, allow_no_convergence=True):
+            return b.detach().clone(), {"outer_iters": 40, "lambda_min_used": 0.01, "lambda_max_used": 2.0,
+                                        "status": "SSTEP_OK"}
+
+        def close(self):
+            pass
+
+    def grad_kappa(h, x, lam, gk):
+        gk.copy_(lam)
+
+    monkeypatch.setattr(pkg, "SStepCG", Solver, raising=False)
+    monkeypatch.setattr(autograd, "SStepCG", Solver)
+    monkeypatch.setattr(abi, "sstep_cg_grad_kappa", grad_kappa)
+    monkeypatch.setattr(abi, "sstep_cg_set_tolerance", lambda *a: None)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "adjoint", "--steps", "2", "--warmup", "1"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_adjoint(bench.parse())
+    d = json.loads([ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")][0])
+    assert d["config"]["workload"] == "adjoint_diffusion2d_1024^2" and d["config"]["n"] == 1024 ** 2
+    assert d["value"] == pytest.approx(EVENT_MS / 2 / 1e3) and d["forward_outer_iters"] == 40
+    gc = d["gradient_check"]
+    assert set(gc) >= {"kind", "fd", "adjoint", "rel_err", "note"} and gc["rel_err"] >= 0
+    for k in ("metric", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "scaling", "dtype", "clocks"):
+        assert k in d, k
