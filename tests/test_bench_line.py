@@ -288,3 +288,53 @@ def test_adjoint_line(fake_gpu, monkeypatch, capsys):
     assert set(gc) >= {"kind", "fd", "adjoint", "rel_err", "note"} and gc["rel_err"] >= 0
     for k in ("metric", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "scaling", "dtype", "clocks"):
         assert k in d, k
+
+
+def test_batch_line(fake_gpu, monkeypatch, capsys):
+    """--workload batch (4 systems, no tuning): the batched solve over the concatenated vectors,
+    the plain loop of single-system solves, and the line's keys."""
+    import numpy as np
+    import paper_2512_09642_gb300 as pkg
+    from paper_2512_09642_gb300 import abi
+    seen = {}
+
+    def create(grids, kappas, opts, stream=None):
+        seen["grids"] = [tuple(g) for g in grids]
+        return object()
+
+    def layout(h, count):
+        sizes = [int(np.prod(g)) for g in seen["grids"]]
+        offs = np.concatenate([[0], np.cumsum([(n + 31) // 32 * 32 for n in sizes])[:-1]]).astype(np.int64)
+        return offs, int(offs[-1] + sizes[-1]), np.tile([0.01, 2.0], (count, 1))
+
+    def solve(h, b, x, count, allow=(5,)):
+        x.copy_(b)
+        info = {"status": "SSTEP_OK", "outer_iters": 30, "rel_res_true": 5e-9}
+        return [dict(info) for _ in range(count)], dict(info)
+
+    class Solver:
+        def __init__(self, **kw):
+            self.h = object()
+
+        def solve_into(self, b, x):
+            x.copy_(b)
+            return {"outer_iters": 25, "status": "SSTEP_OK"}
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(abi, "sstep_cg_batch_create", create)
+    monkeypatch.setattr(abi, "sstep_cg_batch_layout", layout)
+    monkeypatch.setattr(abi, "sstep_cg_batch_solve", solve)
+    monkeypatch.setattr(abi, "sstep_cg_batch_destroy", lambda h: None)
+    monkeypatch.setattr(pkg, "SStepCG", Solver, raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "batch", "--batch-count", "4", "--no-tune",
+                                      "--steps", "2", "--warmup", "1"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_batch(bench.parse())
+    d = json.loads([ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")][0])
+    assert len(seen["grids"]) == 4 and d["config"]["workload"] == "batch_4_diffusion2d_sides32-512"
+    assert d["config"]["n_total"] == sum(int(np.prod(g)) for g in seen["grids"])
+    assert d["value"] == pytest.approx(EVENT_MS / 2 / 1e3)
+    assert d["batch"]["systems_ok"] == 4 and d["batch"]["max_outer_iters"] == 30 and d["batch"]["tuned"] is None
+    assert d["plain_fp64_loop"]["max_outer_iters"] == 25 and d["plain_fp64_loop"]["graph"] is True
