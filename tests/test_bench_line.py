@@ -338,3 +338,24 @@ def test_batch_line(fake_gpu, monkeypatch, capsys):
     assert d["value"] == pytest.approx(EVENT_MS / 2 / 1e3)
     assert d["batch"]["systems_ok"] == 4 and d["batch"]["max_outer_iters"] == 30 and d["batch"]["tuned"] is None
     assert d["plain_fp64_loop"]["max_outer_iters"] == 25 and d["plain_fp64_loop"]["graph"] is True
+
+
+def test_spread_line(fake_gpu, monkeypatch, capsys):
+    """--workload spread: every form on the five seeded x* at both sizes (the grids shrunk to 8^3
+    here), the median time per outer iteration of the headline form at the larger size as the
+    value, and the oracle's stored counts beside the 128^3 runs."""
+    from workloads import problems as W
+    real = W.poisson3d
+    monkeypatch.setattr(W, "poisson3d", lambda side, xstar_seed=None, **kw: real(8, xstar_seed=xstar_seed))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "spread", "--warmup", "1"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.run_spread(bench.parse())
+    d = json.loads([ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")][0])
+    rows = d["spread"]
+    forms = ["fp64+mom", "fp64", "mixed+mom", "mixed"]
+    assert [(r["side"], r["form"]) for r in rows] == [(s, f) for s in (128, 256) for f in forms]
+    for r in rows:
+        assert [x["xstar_seed"] for x in r["runs"]] == list(bench.SPREAD_SEEDS)
+        assert r["outer_min"] <= r["outer_median"] <= r["outer_max"]
+    assert all(x["oracle_outer_iters"] for x in rows[0]["runs"])   # stored oracle counts at 128^3
+    assert d["value"] == pytest.approx(rows[4]["ms_per_outer_median"] / 1e3)
