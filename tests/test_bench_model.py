@@ -138,3 +138,14 @@ def test_kernel_report_dominant_kernel_and_roof():
     infos = [info([1.6, 0.3, 0.4, 0.0], [8, 1, 1, 0])]
     roof, table = bench.kernel_report(args, n, infos, "fp64+mom")
     assert table["residual"]["avg_launch_ms"] is None and table["residual"]["share"] == 0.0
+
+
+def test_every_profile_summary_gives_its_command():
+    """Each summary under profiles/ names the command that produced its figures (a bench.py or
+    ncu line, the build-and-run line of a microbenchmark, or the capture it shares), and runs
+    committed files only."""
+    import glob
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(f).read()
+        assert any(k in text for k in ("python bench.py", "ncu ", "nvcc ", "Same capture as")), f
+        assert "_work" not in text, f
